@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Throughput of the bipartite H|psi> on one GB300 (or N replicas).
+
+Default workload: J1-J2 Heisenberg on the 4x8 torus, J1=1, J2=0.5, Sz=0
+(601,080,390 states, 17 blocks, cut 16|16), FP64 storage.  One step = one
+H|psi> of the whole sector vector (input and output 4.8 GB each, far larger
+than L2, so no flush is needed between steps).  The JSON line also carries
+the FP32 H|psi> rate, Lanczos time-to-E0 for plain FP64 vs mixed precision,
+an end-to-end rate through the C ABI with host buffers, the roofline of the
+apply kernel and the oracle's CPU rate on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "H psi/s & HBM GB/s vs peak, 4x8 J1-J2 Sz=0; time-to-E0(1e-10) mixed vs FP64"
+UNIT = "Hpsi/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="j1j2_4x8", choices=list(W.CONFIG_NAMES))
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    p.add_argument("--no-lanczos", action="store_true", help="skip the time-to-E0 comparison")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--lanczos-max-iter", type=int, default=400)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("apply.cu", "ed_internal.h", "ops.cpp"):
+        with open(os.path.join(ROOT, "paper_2605_07621_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        load = sorted(sm)
+        return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(model, budget_s: float = 12.0):
+    """The oracle's H|psi> rows on the host cores, bounded sample, scaled to H psi/s."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.time()
+    keys = oracle.sector_keys(model)
+    t_keys = time.time() - t0
+    D = len(keys)
+    x = np.ones(D)
+    probe = min(D, 20000)
+    t0 = time.time()
+    oracle.apply_H_rows(model, keys, x, 0, probe, nthreads=cores)
+    dt = max(time.time() - t0, 1e-6)
+    rows = int(min(D, max(probe, probe * budget_s / dt)))
+    t0 = time.time()
+    oracle.apply_H_rows(model, keys, x, 0, rows, nthreads=cores)
+    dt = time.time() - t0
+    return {"value": (rows / D) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"rows 0..{rows} of {D} ({rows / D:.2e} of one H psi), full sector key list "
+                      f"({t_keys:.1f} s to enumerate, not timed), all threads"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    model = W.config_by_name(args.config)
+    cores = len(os.sched_getaffinity(0))
+    keys = oracle.sector_keys(model)
+    D = len(keys)
+    x = np.ones(D)
+    probe = min(D, 20000)
+    t0 = time.time()
+    oracle.apply_H_rows(model, keys, x, 0, probe, nthreads=cores)
+    rate = probe / max(time.time() - t0, 1e-6)
+    rows = int(min(D, max(probe, rate * 8.0)))  # ~8 s per step
+    for _ in range(args.warmup):
+        oracle.apply_H_rows(model, keys, x, 0, rows, nthreads=cores)
+    t0 = time.time()
+    for _ in range(args.steps):
+        oracle.apply_H_rows(model, keys, x, 0, rows, nthreads=cores)
+    dt = time.time() - t0
+    value = args.steps * (rows / D) / dt
+    sample = f"each step: rows 0..{rows} of {D} of one H psi ({rows / D:.2e}), scaled to H psi/s"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.config, "states": D, "l2_flush": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2605_07621_gb300 as ed
+
+    model = W.config_by_name(args.config)
+    t0 = time.time()
+    ctx = ed.build_local_ops(ed.build_sectors(model))
+    t_setup = time.time() - t0
+    D = ctx.dim
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    esz = 8 if args.dtype == "f64" else 4
+    stream = torch.cuda.current_stream()
+    x = torch.empty(D, dtype=torch.float64, device=dev)
+    ed.random_vector(ctx, x, seed=W.DEFAULT_SEED)
+    if tdt != torch.float64:
+        x = x.to(tdt)
+    y = torch.empty_like(x)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        ed.apply_H(ctx, x, y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ed.apply_H(ctx, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    t_max = ms
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = ws * args.steps / (t_max / 1000.0)
+
+    # the other precision, same workload (not part of the headline)
+    other = {}
+    odt = torch.float32 if tdt == torch.float64 else torch.float64
+    xo = x.to(odt)
+    yo = torch.empty_like(xo)
+    for _ in range(2):
+        ed.apply_H(ctx, xo, yo)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(3, args.steps // 2)):
+        ed.apply_H(ctx, xo, yo)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    oms = e0.elapsed_time(e1) / max(3, args.steps // 2)
+    other = {"dtype": "f32" if odt == torch.float32 else "f64", "hpsi_per_s": 1000.0 / oms, "ms_per_hpsi": oms,
+             "algorithmic_gbs": 2 * D * (4 if odt == torch.float32 else 8) / (oms * 1e-3) / 1e9}
+    del xo, yo
+
+    peaks, peak_src = measured_peaks()
+    alg_bytes = 2 * D * esz
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        ent = tr.get(f"{args.config}:{args.dtype}")
+        if ent and ent.get("kernel_hash") == kernel_source_hash():
+            traffic = ent["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src,
+            "kernel": "k_apply_rows", "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the C ABI with host buffers: H2D x, H psi, D2H y
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(D, dtype=tdt, pin_memory=True)
+        yh = torch.empty(D, dtype=tdt, pin_memory=True)
+        xh.copy_(x)
+        n_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(n_e2e):
+            x.copy_(xh, non_blocking=True)
+            ed.apply_H(ctx, x, y)
+            yh.copy_(y, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e = {"value": n_e2e / wall, "unit": UNIT, "h2d_bytes_per_step": D * esz, "d2h_bytes_per_step": D * esz,
+               "device_ms_per_step": e0.elapsed_time(e1) / n_e2e}
+        del xh, yh
+
+    # Lanczos time-to-E0: plain FP64 vs FP32 + FP64 refinement
+    lanczos = None
+    if not args.no_lanczos and rank == 0:
+        del x, y
+        torch.cuda.empty_cache()
+        lanczos = {}
+        for mode in ("f64", "mixed"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ed.lanczos_ground(ctx, mode=mode, tol=1e-12, max_iter=args.lanczos_max_iter)
+            wall = time.perf_counter() - t0
+            lanczos[mode] = {"e0": r.e0, "seconds": wall, "iterations": r.iterations,
+                             "iterations_fp32": r.iterations_low, "restarts": r.restarts,
+                             "converged": r.converged}
+        lanczos["mixed_vs_f64_rel"] = abs(lanczos["mixed"]["e0"] - lanczos["f64"]["e0"]) / abs(lanczos["f64"]["e0"])
+        lanczos["speedup_mixed"] = lanczos["f64"]["seconds"] / lanczos["mixed"]["seconds"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline(model)
+        except Exception as exc:  # the baseline must not hide the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                   "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": args.config, "states": D, "blocks": ctx.num_blocks,
+                           "parallelism": "replicas" if ws > 1 else "single", "l2_flush": "inputs larger than L2",
+                           "setup_s": t_setup},
+                "gpu_launches": args.steps,
+                "roofline": roof, "clocks": clk, "e2e": e2e, "other_precision": other, "lanczos": lanczos,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

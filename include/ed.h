@@ -1,0 +1,173 @@
+/*
+ * ed.h -- C ABI of the GB300 bipartite H|psi> / Lanczos engine.
+ *
+ * The wavefunction of one symmetry sector of a K-local lattice model
+ * (paper Eq. (1)) is stored in the entanglement-cut representation of
+ * Eq. (3): a set of symmetry-resolved blocks Psi_s, one per value s of the
+ * conserved charge on side A of the cut, each a d_A(s) x d_B(s) matrix.  The
+ * Hamiltonian has the block form of Eq. (2):
+ *     (H psi)_s = H_A,s Psi_s + Psi_s H_B,s^T + V_s o Psi_s
+ *                 + sum_k c_k P^A_k Psi_s' (P^B_k)^T
+ * (side Hamiltonians, a diagonal, and the cross-cut terms evaluated through
+ * the paper's Vec/Kronecker identity [L (x) R] Vec(Psi) = Vec(R Psi L^T)).
+ *
+ * Vector layout (every x, y, psi pointer below): blocks concatenated in
+ * ascending s; block s is row-major d_A(s) x d_B(s) (B index contiguous),
+ * starting at element offset off[s] (ed_blocks).  Rows are the side-A
+ * states of charge s in ascending bit-string order (combinadic / colex
+ * rank), columns the side-B states likewise.  Bit p of a side-A string is
+ * the p-th site of the A side in ascending site order (Hubbard spin cut:
+ * side A = spin-up occupations, side B = spin-down occupations).
+ *
+ * Ownership: the caller owns every vector it passes (device pointers unless
+ * stated); the context owns all operator tables, maps and work buffers.
+ * Errors: every call returns an ed_status and never aborts; ed_last_error()
+ * gives a message for the calling thread.  Streams: the caller's stream is
+ * used; no call synchronises the device except where it returns host
+ * scalars (noted per call).
+ */
+#ifndef ED_H
+#define ED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ed_ctx ed_ctx;
+
+typedef enum {
+  ED_OK = 0,
+  ED_EINVAL = 1,       /* malformed model, bad argument or size */
+  ED_ENOMEM = 2,       /* device or host allocation failed */
+  ED_ECUDA = 3,        /* a CUDA runtime call failed */
+  ED_ENOCONV = 4,      /* Lanczos stopped at max_iter without meeting tol */
+  ED_ETIMEOUT = 5,     /* a bounded wait ran out */
+  ED_EUNSUPPORTED = 6, /* valid request outside what this build supports */
+  ED_ECANCELLED = 7    /* a served request was cancelled */
+} ed_status;
+
+typedef enum { ED_F64 = 0, ED_F32 = 1 } ed_dtype;
+
+typedef enum { ED_SPIN = 0, ED_HUBBARD = 1 } ed_kind;
+
+/* One lattice model, its target sector and its entanglement cut.
+ * Spin (ED_SPIN): H = sum_b [ jz_b S^z_i S^z_j + jxy_b/2 (S^+_i S^-_j + h.c.) ],
+ *   n_up = number of up spins; cut_mask = bit mask of side-A sites.
+ * Hubbard (ED_HUBBARD): H = -sum_{b,sigma} t_b (c^dag_i c_j + h.c.)
+ *   + sum_i U_i n_i,up n_i,dw + sum_i eps_i n_i; sector (n_up, n_dw); the cut
+ *   separates spin up (side A) from spin down (side B), spin_cut must be 1.
+ *   Fermion order: all up sites ascending, then all down sites ascending.
+ * All arrays are host memory, read during ed_build_sectors only. */
+typedef struct {
+  int kind;
+  int n_sites;             /* 1 .. 64 (spin), 1 .. 32 (Hubbard) */
+  int n_bonds;
+  const int* bi;           /* bond endpoints, length n_bonds */
+  const int* bj;
+  const double* jxy;       /* spin, per bond (NULL = 0) */
+  const double* jz;        /* spin, per bond (NULL = 0) */
+  const double* t;         /* Hubbard, per bond (NULL = 0) */
+  const double* U;         /* Hubbard, per site (NULL = 0) */
+  const double* eps;       /* Hubbard, per site (NULL = 0) */
+  int n_up;
+  int n_dw;
+  uint64_t cut_mask;       /* spin: side-A sites; each side at most 30 sites */
+  int spin_cut;            /* Hubbard: 1 */
+} ed_model_desc;
+
+/* Build the sector/block structure (paper Eqs. (2)-(3): charges q_l + q_r
+ * = q, block dimensions and offsets, combinadic ranks).  Selects the
+ * current CUDA device for the context.  *out is set on success. */
+ed_status ed_build_sectors(const ed_model_desc* model, ed_ctx** out);
+
+/* Build the side operators of Eq. (2) on the device: CSR of H_A,s and
+ * H_B,s off-diagonals, side diagonals, the cross-cut maps.
+ * flags: ED_OPS_DEFAULT, or ED_OPS_FORCE_CSR / ED_OPS_FORCE_DENSE to pin the
+ * per-sector choice instead of autotuning it.  Synchronises the device. */
+#define ED_OPS_DEFAULT 0
+#define ED_OPS_FORCE_CSR 1
+#define ED_OPS_FORCE_DENSE 2
+ed_status ed_build_local_ops(ed_ctx* ctx, int flags);
+
+/* y = H x over the whole sector (all blocks), device pointers of ed_dim
+ * elements of `dtype`, x and y must not overlap.  ED_F64: FP64 storage,
+ * FP64-accurate result; ED_F32: FP32 storage and accumulation.  Enqueued on
+ * `stream` (cudaStream_t, NULL = legacy default stream); no sync. */
+ed_status ed_apply_H(ed_ctx* ctx, const void* x, void* y, ed_dtype dtype, void* stream);
+
+/* Lanczos options / report (paper: H|psi> as the kernel of a Krylov
+ * solver).  mode: ED_LZ_F64 plain FP64; ED_LZ_F32 FP32 storage with FP64
+ * reductions; ED_LZ_MIXED FP32 Lanczos then FP64 restarted refinement until
+ * the energy is stable to tol. */
+typedef enum { ED_LZ_F64 = 0, ED_LZ_F32 = 1, ED_LZ_MIXED = 2 } ed_lz_mode;
+
+typedef struct {
+  int mode;              /* ed_lz_mode */
+  int max_iter;          /* Lanczos steps cap (per phase); default 400 */
+  double tol;            /* relative change of the lowest Ritz value; default 1e-12 */
+  int check_every;       /* convergence test period in steps; default 5 */
+  int fixed_iter;        /* 1: run exactly max_iter steps, no convergence stop */
+  int reorth;            /* 1: full reorthogonalisation when the basis fits */
+  uint64_t seed;         /* start vector = key-indexed SplitMix64 values */
+  const double* v0;      /* optional FP64 device start vector (overrides seed) */
+  int refine_block;      /* mixed mode: steps per FP64 restart; default 30 */
+  void* stream;          /* cudaStream_t */
+} ed_lanczos_opts;
+
+typedef struct {
+  int iterations;        /* total Lanczos steps (all phases) */
+  int iterations_low;    /* steps taken in FP32 storage (mixed / f32) */
+  int restarts;          /* FP64 restarts (mixed) */
+  int converged;         /* 1 if tol was met */
+  double e_low;          /* energy after the FP32 phase (mixed) */
+  double residual;       /* ||H psi - E psi|| in FP64 (when a vector was formed) */
+  double seconds;        /* wall time of the call */
+  double* alpha;         /* optional host buffers (capacity ab_capacity) for */
+  double* beta;          /*   the first-phase coefficients alpha_j, beta_{j+1} */
+  int ab_capacity;
+  int n_ab;              /* number of alpha written */
+} ed_report;
+
+void ed_lanczos_default_opts(ed_lanczos_opts* o);
+
+/* Lowest eigenvalue E0 of the sector (and optionally its FP64 eigenvector
+ * into psi0, device, ed_dim doubles).  Synchronises the stream.  Returns
+ * ED_ENOCONV (with *e0 and the report filled) when tol was not met. */
+ed_status ed_lanczos_ground(ed_ctx* ctx, const ed_lanczos_opts* opts, double* e0, void* psi0, ed_report* rep);
+
+/* Zero-temperature Green's function of a Hubbard context:
+ *   G(w) = <psi0| c (z - (H - E0))^-1 c^dag |psi0> + <psi0| c^dag (z + (H - E0))^-1 c |psi0>,
+ * z = w + i eta, c = c_{site,spin} (spin 0 = up), from n_iter-step FP64
+ * Lanczos continued fractions started from c^dag psi0 and c psi0 (built on
+ * the device in the shifted sectors).  psi0: device FP64 ground state of
+ * ctx; omega: host, n_omega; G: host, 2*n_omega doubles (re, im pairs).
+ * a_p, b_p, a_h, b_h: optional host outputs (n_iter each) of the particle
+ * and hole coefficients; w_p, w_h: optional norms ||c^dag psi0||^2,
+ * ||c psi0||^2.  Synchronises the stream. */
+ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int spin, int n_iter,
+                        const double* omega, int n_omega, double eta, double* G, double* a_p, double* b_p,
+                        double* a_h, double* b_h, double* w_p, double* w_h, void* stream);
+
+/* ---- queries ---------------------------------------------------------- */
+int64_t ed_dim(const ed_ctx* ctx);
+int ed_num_blocks(const ed_ctx* ctx);
+/* per block: charge s, d_A, d_B, element offset (host arrays of ed_num_blocks) */
+ed_status ed_blocks(const ed_ctx* ctx, int* s, int64_t* dA, int64_t* dB, int64_t* off);
+/* bit-string keys (oracle convention: spin key bit i = site i; Hubbard
+ * key = up | dw << n_sites) of the global indices [start, start+count), host. */
+ed_status ed_state_keys(const ed_ctx* ctx, int64_t start, int64_t count, uint64_t* keys);
+/* fill x (device, ed_dim elements of dtype) with the key-indexed SplitMix64
+ * values U[-1,1) for `seed` (unnormalised); enqueued on stream. */
+ed_status ed_random_vector(ed_ctx* ctx, uint64_t seed, void* x, ed_dtype dtype, void* stream);
+/* device memory held by the context, bytes */
+int64_t ed_device_bytes(const ed_ctx* ctx);
+void ed_destroy(ed_ctx* ctx);
+const char* ed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ED_H */

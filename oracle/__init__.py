@@ -14,6 +14,7 @@ from .ed import (  # noqa: F401
     sector_keys,
     sector_dim,
     apply_H,
+    apply_H_rows,
     dense_H,
     row_terms,
     find_keys,

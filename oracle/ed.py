@@ -79,6 +79,9 @@ def _get():
         lib.or_apply.restype = ctypes.c_int
         lib.or_apply.argtypes = [P(_OrModel), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_int]
+        lib.or_apply_range.restype = ctypes.c_int
+        lib.or_apply_range.argtypes = [P(_OrModel), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
         lib.or_dense.restype = ctypes.c_int
         lib.or_dense.argtypes = [P(_OrModel), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         lib.or_rows.restype = ctypes.c_int64
@@ -155,6 +158,18 @@ def apply_H(model, keys: np.ndarray, x: np.ndarray, nthreads: int = 0) -> np.nda
     if _get().or_apply(ref.ptr, keys.ctypes.data, len(keys), x.ctypes.data, y.ctypes.data, int(nthreads)) != 0:
         raise RuntimeError("oracle: H connects a state outside the sector basis")
     return y
+
+
+def apply_H_rows(model, keys: np.ndarray, x: np.ndarray, r0: int, r1: int, nthreads: int = 0) -> np.ndarray:
+    """Rows [r0, r1) of y = H x (same arithmetic as ``apply_H``)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(max(r1 - r0, 1), dtype=np.float64)
+    ref = _ModelRef(model)
+    if _get().or_apply_range(ref.ptr, keys.ctypes.data, len(keys), x.ctypes.data, int(r0), int(r1), y.ctypes.data,
+                             int(nthreads)) != 0:
+        raise RuntimeError("oracle: H connects a state outside the sector basis")
+    return y[: r1 - r0]
 
 
 def dense_H(model, keys: np.ndarray) -> np.ndarray:

@@ -206,10 +206,11 @@ int or_find(const or_model* m, const uint64_t* keys, int64_t D, const uint64_t* 
 
 #define ROW_CAP 512
 
-/* y = H x on the full sector with sorted basis `keys` (length D).
- * Returns 0, or -1 if a connected state is missing from the basis
- * (which would mean H leaves the sector). */
-int or_apply(const or_model* m, const uint64_t* keys, int64_t D, const double* x, double* y, int nthreads) {
+/* Rows [r0, r1) of y = H x on the full sector with sorted basis `keys`
+ * (length D); y has r1 - r0 entries.  Returns 0, or -1 if a connected state
+ * is missing from the basis (which would mean H leaves the sector). */
+int or_apply_range(const or_model* m, const uint64_t* keys, int64_t D, const double* x, int64_t r0, int64_t r1,
+                   double* y, int nthreads) {
   or_index ix;
   index_build(&ix, m, keys, D);
   int bad = 0;
@@ -223,7 +224,7 @@ int or_apply(const or_model* m, const uint64_t* keys, int64_t D, const double* x
     uint64_t nk[ROW_CAP];
     double nv[ROW_CAP];
 #pragma omp for schedule(static)
-    for (int64_t r = 0; r < D; ++r) {
+    for (int64_t r = r0; r < r1; ++r) {
       double diag;
       int c = or_row(m, keys[r], &diag, nk, nv, ROW_CAP);
       if (c < 0) { bad = 1; continue; }
@@ -233,11 +234,16 @@ int or_apply(const or_model* m, const uint64_t* keys, int64_t D, const double* x
         if (col < 0) { bad = 1; continue; }
         acc += nv[e] * x[col];
       }
-      y[r] = acc;
+      y[r - r0] = acc;
     }
   }
   index_free(&ix);
   return bad ? -1 : 0;
+}
+
+/* y = H x on the full sector (all rows). */
+int or_apply(const or_model* m, const uint64_t* keys, int64_t D, const double* x, double* y, int nthreads) {
+  return or_apply_range(m, keys, D, x, 0, D, y, nthreads);
 }
 
 /* Dense H (row-major D x D) for small sectors. */

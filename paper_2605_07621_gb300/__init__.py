@@ -1,0 +1,25 @@
+"""GB300-native bipartite (entanglement-cut) H|psi>, Lanczos and Green's-function engine.
+
+``paper_2605_07621_gb300.ed`` is the Python binding of the C ABI in
+``include/ed.h``; the compute runs only in the CUDA library built by
+``paper_2605_07621_gb300.build`` (there is no CPU fallback: importing the
+binding without the built library raises ImportError).
+"""
+from . import _lib
+
+_lib.load()
+
+from .ed import (  # noqa: E402,F401
+    Context,
+    LanczosResult,
+    apply_H,
+    build_local_ops,
+    build_sectors,
+    lanczos_gf,
+    lanczos_ground,
+    random_vector,
+)
+from ._lib import EDError  # noqa: E402,F401
+
+__all__ = ["Context", "LanczosResult", "apply_H", "build_local_ops", "build_sectors", "lanczos_gf",
+           "lanczos_ground", "random_vector", "EDError"]

@@ -1,0 +1,234 @@
+"""Python binding of the C ABI (include/ed.h) with the same names.
+
+Argument marshalling only: every step runs in the CUDA library.  PyTorch
+provides device memory and streams; vectors are CUDA tensors laid out as the
+C ABI describes (blocks Psi_s concatenated, each row-major d_A x d_B).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+_MODES = {"f64": L.ED_LZ_F64, "f32": L.ED_LZ_F32, "mixed": L.ED_LZ_MIXED}
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns an ``ed_ctx*``; destroyed with the object."""
+
+    def __init__(self, handle: int, model):
+        self._h = ctypes.c_void_p(handle)
+        self.model = model
+        self._ops = False
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            L.load().ed_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dim(self) -> int:
+        return int(L.load().ed_dim(self._h))
+
+    @property
+    def num_blocks(self) -> int:
+        return int(L.load().ed_num_blocks(self._h))
+
+    def blocks(self):
+        """(s, d_A, d_B, offset) arrays, one entry per block."""
+        n = self.num_blocks
+        s = np.zeros(n, np.int32)
+        dA = np.zeros(n, np.int64)
+        dB = np.zeros(n, np.int64)
+        off = np.zeros(n, np.int64)
+        L.check(L.load().ed_blocks(self._h, s.ctypes.data, dA.ctypes.data, dB.ctypes.data, off.ctypes.data))
+        return s, dA, dB, off
+
+    def state_keys(self, start: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.dim - start
+        keys = np.empty(max(count, 1), np.uint64)
+        L.check(L.load().ed_state_keys(self._h, int(start), int(count), keys.ctypes.data))
+        return keys[:count]
+
+    @property
+    def device_bytes(self) -> int:
+        return int(L.load().ed_device_bytes(self._h))
+
+
+def model_desc(model):
+    """ed_model_desc from any object with the fields of ``workloads.Model``;
+    returns (desc, keepalive)."""
+    kind = L.ED_SPIN if model.kind == "spin" else L.ED_HUBBARD
+    bonds = np.ascontiguousarray(np.asarray(model.bonds, dtype=np.int32).reshape(-1, 2))
+    keep = {
+        "bi": np.ascontiguousarray(bonds[:, 0]),
+        "bj": np.ascontiguousarray(bonds[:, 1]),
+        "jxy": np.ascontiguousarray(model.jxy, dtype=np.float64),
+        "jz": np.ascontiguousarray(model.jz, dtype=np.float64),
+        "t": np.ascontiguousarray(model.t, dtype=np.float64),
+        "U": np.ascontiguousarray(model.U, dtype=np.float64),
+        "eps": np.ascontiguousarray(model.eps, dtype=np.float64),
+    }
+    P = ctypes.POINTER
+    d = L.ModelDesc()
+    d.kind = kind
+    d.n_sites = int(model.n_sites)
+    d.n_bonds = len(bonds)
+    d.bi = keep["bi"].ctypes.data_as(P(ctypes.c_int))
+    d.bj = keep["bj"].ctypes.data_as(P(ctypes.c_int))
+    for f in ("jxy", "jz", "t", "U", "eps"):
+        setattr(d, f, keep[f].ctypes.data_as(P(ctypes.c_double)))
+    d.n_up = int(model.n_up)
+    d.n_dw = int(model.n_dw)
+    d.cut_mask = int(model.cut_mask) & 0xFFFFFFFFFFFFFFFF
+    d.spin_cut = 1 if model.spin_cut else 0
+    return d, keep
+
+
+def build_sectors(model) -> Context:
+    d, keep = model_desc(model)
+    h = ctypes.c_void_p()
+    L.check(L.load().ed_build_sectors(ctypes.byref(d), ctypes.byref(h)))
+    return Context(h.value, model)
+
+
+def build_local_ops(ctx: Context, flags: int = 0) -> Context:
+    L.check(L.load().ed_build_local_ops(ctx.handle, int(flags)))
+    ctx._ops = True
+    return ctx
+
+
+def _check_vec(ctx, t, name, dtype=None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous() or t.numel() != ctx.dim:
+        raise ValueError(f"{name} must be contiguous with {ctx.dim} elements")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+
+
+def apply_H(ctx: Context, x, y, stream=None):
+    """y = H x (both CUDA tensors, float64 or float32)."""
+    import torch
+
+    _check_vec(ctx, x, "x")
+    _check_vec(ctx, y, "y", x.dtype)
+    dt = {torch.float64: L.ED_F64, torch.float32: L.ED_F32}.get(x.dtype)
+    if dt is None:
+        raise TypeError("x must be float64 or float32")
+    L.check(L.load().ed_apply_H(ctx.handle, _ptr(x), _ptr(y), dt, _stream_handle(stream)))
+    return y
+
+
+def random_vector(ctx: Context, x, seed: int = 20260507, stream=None):
+    import torch
+
+    _check_vec(ctx, x, "x")
+    dt = {torch.float64: L.ED_F64, torch.float32: L.ED_F32}[x.dtype]
+    L.check(L.load().ed_random_vector(ctx.handle, ctypes.c_uint64(seed), _ptr(x), dt, _stream_handle(stream)))
+    return x
+
+
+@dataclass
+class LanczosResult:
+    e0: float
+    iterations: int
+    iterations_low: int
+    restarts: int
+    converged: bool
+    e_low: float
+    residual: float
+    seconds: float
+    alpha: np.ndarray
+    beta: np.ndarray
+    status: int
+
+
+def lanczos_ground(ctx: Context, mode: str = "f64", max_iter: int = 400, tol: float = 1e-12, check_every: int = 5,
+                   fixed_iter: bool = False, reorth: bool = False, seed: int = 20260507, v0=None, psi0=None,
+                   refine_block: int = 30, stream=None, ab_capacity: int = 1024, raise_on_noconv: bool = False):
+    """Lowest eigenvalue (and optionally eigenvector into ``psi0``, a float64 CUDA tensor)."""
+    o = L.LanczosOpts()
+    L.load().ed_lanczos_default_opts(ctypes.byref(o))
+    o.mode = _MODES[mode]
+    o.max_iter = int(max_iter)
+    o.tol = float(tol)
+    o.check_every = int(check_every)
+    o.fixed_iter = 1 if fixed_iter else 0
+    o.reorth = 1 if reorth else 0
+    o.seed = int(seed)
+    o.refine_block = int(refine_block)
+    o.stream = _stream_handle(stream)
+    if v0 is not None:
+        import torch
+
+        _check_vec(ctx, v0, "v0", torch.float64)
+        o.v0 = v0.data_ptr()
+    if psi0 is not None:
+        import torch
+
+        _check_vec(ctx, psi0, "psi0", torch.float64)
+    a = np.zeros(ab_capacity)
+    b = np.zeros(ab_capacity)
+    r = L.Report()
+    r.alpha = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.beta = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.ab_capacity = ab_capacity
+    e0 = ctypes.c_double()
+    st = L.load().ed_lanczos_ground(ctx.handle, ctypes.byref(o), ctypes.byref(e0), _ptr(psi0), ctypes.byref(r))
+    if st != L.ED_OK and (st != L.ED_ENOCONV or raise_on_noconv):
+        L.check(st)
+    return LanczosResult(e0.value, r.iterations, r.iterations_low, r.restarts, bool(r.converged), r.e_low,
+                         r.residual, r.seconds, a[: r.n_ab].copy(), b[: r.n_ab].copy(), st)
+
+
+def lanczos_gf(ctx: Context, psi0, e0: float, omega, eta: float, site: int = 0, spin: int = 0, n_iter: int = 300,
+               stream=None):
+    """G(omega + i eta) (complex numpy array) and the Lanczos coefficients."""
+    import torch
+
+    _check_vec(ctx, psi0, "psi0", torch.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    G = np.zeros(2 * len(om))
+    ap, bp, ah, bh = (np.zeros(n_iter) for _ in range(4))
+    wp, wh = ctypes.c_double(), ctypes.c_double()
+    L.check(L.load().ed_lanczos_gf(ctx.handle, _ptr(psi0), float(e0), int(site), int(spin), int(n_iter),
+                                   om.ctypes.data, len(om), float(eta), G.ctypes.data, ap.ctypes.data,
+                                   bp.ctypes.data, ah.ctypes.data, bh.ctypes.data, ctypes.addressof(wp),
+                                   ctypes.addressof(wh), _stream_handle(stream)))
+    coeffs = {"particle": (wp.value, ap, bp), "hole": (wh.value, ah, bh)}
+    return G[0::2] + 1j * G[1::2], coeffs

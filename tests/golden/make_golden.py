@@ -1,0 +1,94 @@
+"""Write the stored expected values under tests/golden/ from the oracle only.
+
+    python tests/golden/make_golden.py
+
+Every number written here comes from ``oracle/`` (full-sector exact
+diagonalisation, FP64 Lanczos with full reorthogonalisation, continued
+fractions) on the seeded workloads of ``workloads/``.  Nothing is taken from
+the CUDA path.
+"""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+
+OUT = os.path.dirname(os.path.abspath(__file__))
+
+
+def _oracle_rev():
+    try:
+        return subprocess.run(["git", "-C", ROOT, "log", "-1", "--format=%H", "--", "oracle"], capture_output=True,
+                              text=True).stdout.strip()
+    except Exception:
+        return ""
+
+
+def heis16():
+    m = W.config_heis16()
+    keys = oracle.sector_keys(m)
+    e0, psi, _ = oracle.ground_state(m, keys, n_iter=300)
+    v0 = W.start_values(keys, W.DEFAULT_SEED)
+    mv = lambda x: oracle.apply_H(m, keys, x)
+    a, b, _ = oracle.lanczos(mv, v0, 150, reorth=False)
+    e150, _ = oracle.tridiag_lowest(a, b[: len(a) - 1])
+    return {"config": "heis16", "e0": e0, "e0_150_noreorth": e150, "alpha_0_19": a[:20].tolist(),
+            "beta_1_20": b[:20].tolist(), "seed": W.DEFAULT_SEED}
+
+
+def hub12():
+    m = W.config_hub12()
+    keys = oracle.sector_keys(m)
+    t = time.time()
+    e0, psi, _ = oracle.ground_state(m, keys, n_iter=300, tol=1e-14)
+    omega = np.linspace(-15.0, 15.0, 2048)
+    G, co = oracle.green_function(m, psi, e0, omega, 0.05, site=0, spin=0, n_iter=300, keys=keys, reorth=True,
+                                  return_coeffs=True)
+    return {"config": "hub12", "e0": e0, "eta": 0.05, "n_iter": 300, "omega": [-15.0, 15.0, 2048],
+            "G_re": G.real.tolist(), "G_im": G.imag.tolist(),
+            "w_particle": co["particle"][0], "w_hole": co["hole"][0],
+            "a_particle_0_29": co["particle"][1][:30].tolist(), "b_particle_1_30": co["particle"][2][:30].tolist(),
+            "seconds": time.time() - t}
+
+
+def small_models():
+    """E0 of small models used by the GPU driver tests (dense brute force)."""
+    rng = np.random.default_rng(11)
+    ms = {
+        "j1j2_4x4": W.j1j2_torus(4, 4, cut_mask=0xFF),
+        "hub_open_3x4": W.hubbard_open_cluster(3, 4, 1.0, 6.0, tp=-0.2, eps=rng.uniform(-1, 1, 12), n_up=5, n_dw=7),
+    }
+    out = {}
+    for k, m in ms.items():
+        keys = oracle.sector_keys(m)
+        e0, _, _ = oracle.ground_state(m, keys, n_iter=400, tol=1e-14)
+        out[k] = e0
+    return out
+
+
+def main():
+    rev = _oracle_rev()
+    for name, fn in (("heis16", heis16), ("hub12", hub12)):
+        d = fn()
+        d["oracle_rev"] = rev
+        with open(os.path.join(OUT, f"{name}.json"), "w") as f:
+            json.dump(d, f, indent=1)
+        print(name, d["e0"])
+    d = {"e0": small_models(), "oracle_rev": rev}
+    with open(os.path.join(OUT, "small_e0.json"), "w") as f:
+        json.dump(d, f, indent=1)
+    print(d)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+"""GPU parity of H|psi> (through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 storage -> relative L2 <= 1e-12; FP32 storage (input is
+the FP32 rounding of the FP64 vector, compared with the oracle applied to
+the FP64 vector) -> relative L2 <= 1e-6.  Outputs are matched to the
+oracle's ordering by bit-string key.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ed():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_07621_gb300 as ed
+
+    return ed
+
+
+def _models():
+    rng = np.random.default_rng(11)
+    return {
+        "heis16": W.config_heis16(),
+        "hub12": W.config_hub12(),
+        "j1j2_4x4": W.j1j2_torus(4, 4, cut_mask=0xFF),
+        "j1j2_4x4_strip": W.j1j2_torus(4, 4, cut_mask=0b0011001100110011),
+        "xxz_odd_cut": W.xxz_chain(11, 1.0, 0.5, n_up=4, cut_mask=0b10110100101),
+        "xxz_n_up_1": W.xxz_chain(9, 0.7, 1.3, n_up=1),
+        "all_on_A": W.heisenberg_chain(10, cut_mask=0x3FF),
+        "all_on_B": W.heisenberg_chain(10, cut_mask=0),
+        "hub_tp_eps": W.hubbard_chain(8, 1.0, 3.0, 3, 5, pbc=True, tp=0.27, eps=rng.uniform(-1, 1, 8)),
+        "hub_2x3_torus": W.hubbard_torus(2, 3, 1.0, 5.0, 2, 3),
+        "hub_open_3x4": W.hubbard_open_cluster(3, 4, 1.0, 6.0, tp=-0.2, eps=rng.uniform(-1, 1, 12), n_up=5, n_dw=7),
+        "hub_empty_dw": W.hubbard_chain(7, 1.0, 2.0, 3, 0),
+        "hub_site_U": W.Model("hubbard", 5, W.chain_bonds(5, True), t=1.0, U=[1.0, 2.0, 3.0, 1.0, 0.0],
+                              eps=[0.1, -0.2, 0.3, 0.0, 0.5], n_up=2, n_dw=3, spin_cut=True),
+    }
+
+
+MODELS = _models()
+
+
+def _parity(ed, oracle_mod, m, dtype):
+    import torch
+
+    ctx = ed.build_local_ops(ed.build_sectors(m))
+    keys = ctx.state_keys()
+    okeys = oracle_mod.sector_keys(m)
+    pos = oracle_mod.find_keys(m, okeys, keys)
+    assert (pos >= 0).all()
+    y_ref = oracle_mod.apply_H(m, okeys, W.start_values(okeys))[pos]
+    x64 = torch.tensor(W.start_values(keys), device="cuda")
+    x = x64.to(dtype)
+    y = torch.full_like(x, float("nan"))
+    ed.apply_H(ctx, x, y)
+    torch.cuda.synchronize()
+    yy = y.double().cpu().numpy()
+    return np.linalg.norm(yy - y_ref) / np.linalg.norm(y_ref)
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_apply_fp64(ed, oracle_mod, name):
+    import torch
+
+    assert _parity(ed, oracle_mod, MODELS[name], torch.float64) <= TOL64
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_apply_fp32(ed, oracle_mod, name):
+    import torch
+
+    assert _parity(ed, oracle_mod, MODELS[name], torch.float32) <= TOL32
+
+
+def test_random_vector_matches_input_generator(ed):
+    import torch
+
+    m = MODELS["hub_open_3x4"]
+    ctx = ed.build_local_ops(ed.build_sectors(m))
+    x = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    ed.random_vector(ctx, x, seed=12345)
+    ref = W.start_values(ctx.state_keys(), 12345)
+    assert np.array_equal(x.cpu().numpy(), ref)
+
+
+def test_apply_rejects_bad_args(ed):
+    import torch
+
+    ctx = ed.build_local_ops(ed.build_sectors(MODELS["heis16"]))
+    x = torch.zeros(ctx.dim, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        ed.apply_H(ctx, x, torch.zeros(ctx.dim + 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ed.EDError, match="overlap"):
+        from paper_2605_07621_gb300 import _lib
+
+        _lib.check(_lib.load().ed_apply_H(ctx.handle, x.data_ptr(), x.data_ptr(), 0, None))
+
+
+def _sampled_rows(ed, oracle_mod, m, n_chunks, chunk, seed=20260507):
+    """H x at full size, x = key-indexed start values generated on the GPU;
+    checked on n_chunks random chunks of consecutive rows against the
+    oracle's row terms evaluated with the same key-indexed values."""
+    import torch
+
+    ctx = ed.build_local_ops(ed.build_sectors(m))
+    D = ctx.dim
+    out = {}
+    for dt in (torch.float64, torch.float32):
+        x = torch.empty(D, dtype=torch.float64, device="cuda")
+        ed.random_vector(ctx, x, seed=seed)
+        xd = x.to(dt)
+        del x
+        y = torch.empty_like(xd)
+        ed.apply_H(ctx, xd, y)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(3)
+        starts = np.sort(rng.integers(0, D - chunk, n_chunks))
+        # include both ends of the vector
+        starts[0] = 0
+        starts[-1] = D - chunk
+        idx = (starts[:, None] + np.arange(chunk)[None, :]).ravel()
+        yg = y[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+        keys = np.concatenate([ctx.state_keys(int(s), chunk) for s in starts])
+        diag, off, nk, nv = oracle_mod.row_terms(m, keys)
+        xv = W.start_values(keys, seed)
+        if dt == torch.float32:
+            xv = xv.astype(np.float32).astype(np.float64)
+            xn = W.start_values(nk, seed).astype(np.float32).astype(np.float64)
+        else:
+            xn = W.start_values(nk, seed)
+        contrib = nv * xn
+        yr = diag * xv + np.add.reduceat(np.concatenate([contrib, [0.0]]), off[:-1]) * (np.diff(off) > 0)
+        out[dt] = np.linalg.norm(yg - yr) / np.linalg.norm(yr)
+        del y, xd
+        torch.cuda.empty_cache()
+    return out
+
+
+def test_hub4x4_sampled_rows(ed, oracle_mod):
+    import torch
+
+    err = _sampled_rows(ed, oracle_mod, W.config_hub4x4(), 200, 2000)
+    assert err[torch.float64] <= TOL64
+    assert err[torch.float32] <= TOL32
+
+
+def test_j1j2_4x8_sampled_rows(ed, oracle_mod):
+    import torch
+
+    err = _sampled_rows(ed, oracle_mod, W.config_j1j2_4x8(), 300, 2000)
+    assert err[torch.float64] <= TOL64
+    assert err[torch.float32] <= TOL32

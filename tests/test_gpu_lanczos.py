@@ -1,0 +1,147 @@
+"""GPU Lanczos ground state, mixed-precision refinement and Green's function
+(through the C ABI) against the oracle (stored values in tests/golden/ were
+written by tests/golden/make_golden.py from the oracle only)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def ed():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_07621_gb300 as ed
+
+    return ed
+
+
+def _ctx(ed, m):
+    return ed.build_local_ops(ed.build_sectors(m))
+
+
+def test_heis16_150_steps_alpha_prefix(ed):
+    """Heisenberg ring L=16: exactly 150 steps without reorthogonalisation
+    from the key-indexed start vector; E0 and alpha_0..19 as the oracle."""
+    g = _gold("heis16.json")
+    ctx = _ctx(ed, W.config_heis16())
+    r = ed.lanczos_ground(ctx, mode="f64", max_iter=150, fixed_iter=True)
+    assert r.iterations == 150
+    assert abs(r.e0 - g["e0"]) <= 1e-10 * abs(g["e0"])
+    assert abs(r.e0 - g["e0_150_noreorth"]) <= 1e-10 * abs(g["e0"])
+    assert np.abs(r.alpha[:20] - np.array(g["alpha_0_19"])).max() < 1e-11
+    assert np.abs(r.beta[:20] - np.array(g["beta_1_20"])).max() < 1e-11
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_hub12_ground_state(ed, mode):
+    g = _gold("hub12.json")
+    ctx = _ctx(ed, W.config_hub12())
+    r = ed.lanczos_ground(ctx, mode=mode)
+    assert r.converged
+    assert abs(r.e0 - g["e0"]) <= 1e-10 * abs(g["e0"]), (r.e0, g["e0"])
+
+
+def test_f32_mode_accuracy(ed):
+    g = _gold("hub12.json")
+    ctx = _ctx(ed, W.config_hub12())
+    r = ed.lanczos_ground(ctx, mode="f32", tol=1e-7)
+    assert abs(r.e0 - g["e0"]) <= 1e-6 * abs(g["e0"])
+
+
+@pytest.mark.parametrize("name", ["j1j2_4x4", "hub_open_3x4"])
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_small_models_e0(ed, name, mode):
+    rng = np.random.default_rng(11)
+    ms = {
+        "j1j2_4x4": W.j1j2_torus(4, 4, cut_mask=0xFF),
+        "hub_open_3x4": W.hubbard_open_cluster(3, 4, 1.0, 6.0, tp=-0.2, eps=rng.uniform(-1, 1, 12), n_up=5, n_dw=7),
+    }
+    e_ref = _gold("small_e0.json")["e0"][name]
+    r = ed.lanczos_ground(_ctx(ed, ms[name]), mode=mode)
+    assert abs(r.e0 - e_ref) <= 1e-10 * abs(e_ref)
+
+
+def test_ground_vector(ed, oracle_mod):
+    import torch
+
+    m = W.config_hub12()
+    ctx = _ctx(ed, m)
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(ctx, mode="mixed", psi0=psi)
+    assert r.residual < 1e-6
+    p = psi.cpu().numpy()
+    assert abs(np.linalg.norm(p) - 1) < 1e-12
+    # Rayleigh quotient with the oracle's H, matched by key
+    keys = ctx.state_keys()
+    okeys = oracle_mod.sector_keys(m)
+    pos = oracle_mod.find_keys(m, okeys, keys)
+    po = np.zeros(len(okeys))
+    po[pos] = p
+    rq = po @ oracle_mod.apply_H(m, okeys, po)
+    assert abs(rq - r.e0) <= 1e-10 * abs(r.e0)
+
+
+def test_lanczos_dimension_one(ed):
+    m = W.xxz_chain(6, 1.0, 0.7, n_up=0)
+    r = ed.lanczos_ground(_ctx(ed, m), mode="f64")
+    assert r.converged and abs(r.e0 - 6 * 0.7 / 4) < 1e-14
+
+
+def test_cut_independence_j1j2_4x4(ed):
+    """The same lattice with three different entanglement cuts has the same spectrum."""
+    es = []
+    for mask in (0xFF, 0x0F0F, 0b0101101001011010):
+        r = ed.lanczos_ground(_ctx(ed, W.j1j2_torus(4, 4, cut_mask=mask)), mode="f64")
+        es.append(r.e0)
+    assert max(es) - min(es) < 1e-10 * abs(es[0])
+
+
+def test_hub12_green_function(ed):
+    import torch
+
+    g = _gold("hub12.json")
+    m = W.config_hub12()
+    ctx = _ctx(ed, m)
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(ctx, mode="f64", psi0=psi, tol=1e-14)
+    lo, hi, n = g["omega"]
+    omega = np.linspace(lo, hi, n)
+    G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, g["eta"], site=0, spin=0, n_iter=g["n_iter"])
+    Gref = np.array(g["G_re"]) + 1j * np.array(g["G_im"])
+    assert abs(co["particle"][0] - g["w_particle"]) < 1e-9
+    assert abs(co["hole"][0] - g["w_hole"]) < 1e-9
+    assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-9
+    rel = np.abs(G - Gref).max() / np.abs(Gref).max()
+    assert rel < 1e-8, rel
+
+
+@pytest.mark.parametrize("spin,site", [(0, 0), (1, 3)])
+def test_green_function_lehmann(ed, oracle_mod, spin, site):
+    import torch
+
+    m = W.hubbard_chain(6, 1.0, 4.0, 3, 2, pbc=True, tp=0.1, eps=np.linspace(-0.5, 0.5, 6))
+    omega = np.linspace(-8, 8, 321)
+    Gref, e_dense = oracle_mod.lehmann_green_function(m, omega, 0.05, site=site, spin=spin)
+    ctx = _ctx(ed, m)
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(ctx, mode="f64", psi0=psi, tol=1e-14, reorth=True)
+    assert abs(r.e0 - e_dense) < 1e-11 * abs(e_dense)
+    # n_iter above every shifted-sector dimension: the Krylov space is exhausted
+    # and the continued fraction is exact (the driver reorthogonalises here)
+    G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=site, spin=spin, n_iter=500)
+    assert np.abs(G - Gref).max() < 1e-9 * np.abs(Gref).max()
+    assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-12
