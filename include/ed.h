@@ -134,8 +134,11 @@ typedef struct {
 void ed_lanczos_default_opts(ed_lanczos_opts* o);
 
 /* Lowest eigenvalue E0 of the sector (and optionally its FP64 eigenvector
- * into psi0, device, ed_dim doubles).  Synchronises the stream.  Returns
- * ED_ENOCONV (with *e0 and the report filled) when tol was not met. */
+ * into psi0, device, ed_dim doubles).  Convergence: the lowest Ritz value
+ * changes by at most tol (relative) over check_every steps; when psi0 is
+ * requested the Ritz residual estimate beta_m |s_m| must also be at most
+ * 1e-10 max(1, |E0|).  Synchronises the stream.  Returns ED_ENOCONV (with
+ * *e0 and the report filled) when this was not met within max_iter. */
 ed_status ed_lanczos_ground(ed_ctx* ctx, const ed_lanczos_opts* opts, double* e0, void* psi0, ed_report* rep);
 
 /* Zero-temperature Green's function of a Hubbard context:
@@ -150,6 +153,78 @@ ed_status ed_lanczos_ground(ed_ctx* ctx, const ed_lanczos_opts* opts, double* e0
 ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int spin, int n_iter,
                         const double* omega, int n_omega, double eta, double* G, double* a_p, double* b_p,
                         double* a_h, double* b_h, double* w_p, double* w_h, void* stream);
+
+/* ---- batched form -------------------------------------------------------
+ * Many independent single-block instances (Hubbard models with the spin
+ * cut) packed into one device arena and stepped together: every kernel is
+ * one persistent launch over all (instance, row) or (instance, chunk) work
+ * items of the active instances, and the whole Lanczos step (apply, FP64
+ * reductions, vector update) is one captured CUDA graph replayed each step.
+ * Per instance, H_A is applied from its CSR or, for small d_A, from a dense
+ * d_A x d_A table; the d_A threshold is chosen by timing the batched apply
+ * (ED_OPS_DEFAULT) or pinned by ED_OPS_FORCE_CSR / ED_OPS_FORCE_DENSE.
+ * Vectors are FP32; reductions are FP64-accurate. */
+typedef struct ed_batch ed_batch;
+ed_status ed_batch_create(const ed_model_desc* models, int n, int flags, ed_batch** out);
+/* total elements of the concatenated layout (instance i at off[i]) */
+int64_t ed_batch_dim(const ed_batch* b);
+ed_status ed_batch_offsets(const ed_batch* b, int64_t* off /* n+1, host */);
+/* chosen dense threshold and the timed apply (ms) for thresholds 0,8,16,32,64 */
+ed_status ed_batch_info(const ed_batch* b, int* dense_threshold, float* tune_ms /* 5, nullable */);
+/* y = H x for all instances (device FP32 vectors in the concatenated layout) */
+ed_status ed_batch_apply(ed_batch* b, const void* x, void* y, ed_dtype dtype, void* stream);
+/* ground-state energies of all instances (mode ED_LZ_F32; tol: relative
+ * change of the lowest Ritz value between checks every check_every steps).
+ * e0: host n doubles; iters: host n ints (nullable).  Synchronises. */
+ed_status ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, double* e0, int* iters, ed_report* rep);
+void ed_batch_destroy(ed_batch* b);
+
+/* ---- serving form -------------------------------------------------------
+ * A request loop with continuous batching over the batched engine: a worker
+ * thread admits queued requests in arrival order whenever a slot is free
+ * and the request's tables plus three FP32 Krylov vectors fit in the
+ * device budget (one arena allocated at creation), keeps their Krylov state
+ * resident, steps all admitted requests together, and completes each one
+ * when its lowest Ritz value is stable to tol at a multiple of check_every
+ * steps since its admission (so a result does not depend on the other
+ * requests in the mix).  Requests: Hubbard models with the spin cut. */
+typedef struct ed_server ed_server;
+typedef struct {
+  int64_t device_bytes;       /* arena for tables and Krylov vectors */
+  int max_slots;              /* requests on the device at once (<= 4096) */
+  int max_iter;               /* Lanczos steps per request */
+  int check_every;            /* steps between convergence checks */
+  double tol;                 /* relative change of the lowest Ritz value */
+  uint64_t seed;              /* start vectors (key-indexed SplitMix64) */
+  int inject_alloc_failures;  /* test hook: fail this many admissions with ED_ENOMEM */
+} ed_server_opts;
+typedef struct {
+  double e0;
+  int iterations;
+  int converged;
+  int status;                 /* ed_status of the request */
+  double latency_s;           /* submit -> done */
+  double queue_s;             /* submit -> admitted */
+  double run_s;               /* admitted -> done */
+} ed_result;
+typedef struct {
+  int64_t submitted, completed, failed, queued, running;
+  double p50_s, p99_s, mean_s;    /* latency of completed requests */
+  double throughput_rps;          /* completed / (last completion - first submit) */
+  int64_t device_bytes, device_bytes_free;
+} ed_server_stats;
+void ed_server_default_opts(ed_server_opts* o);
+ed_status ed_server_create(const ed_server_opts* opts, ed_server** out);
+/* queue a request (model arrays are copied); *ticket identifies it */
+ed_status ed_server_submit(ed_server* s, const ed_model_desc* model, uint64_t* ticket);
+/* wait at most timeout_ms for the request: ED_ETIMEOUT if it has not
+ * finished, otherwise the request's status with *res filled */
+ed_status ed_server_wait(ed_server* s, uint64_t ticket, int timeout_ms, ed_result* res);
+/* cancel a queued or running request (it leaves between steps) */
+ed_status ed_server_cancel(ed_server* s, uint64_t ticket);
+ed_status ed_server_get_stats(ed_server* s, ed_server_stats* out);
+/* stops the worker after its current step and frees the device arena */
+void ed_server_destroy(ed_server* s);
 
 /* ---- queries ---------------------------------------------------------- */
 int64_t ed_dim(const ed_ctx* ctx);

@@ -10,8 +10,13 @@ from . import _lib
 _lib.load()
 
 from .ed import (  # noqa: E402,F401
+    Batch,
+    batch_apply,
+    batch_create,
+    batch_lanczos,
     Context,
     LanczosResult,
+    Server,
     apply_H,
     build_local_ops,
     build_sectors,
@@ -21,5 +26,5 @@ from .ed import (  # noqa: E402,F401
 )
 from ._lib import EDError  # noqa: E402,F401
 
-__all__ = ["Context", "LanczosResult", "apply_H", "build_local_ops", "build_sectors", "lanczos_gf",
+__all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "LanczosResult", "Server", "apply_H", "build_local_ops", "build_sectors", "lanczos_gf",
            "lanczos_ground", "random_vector", "EDError"]

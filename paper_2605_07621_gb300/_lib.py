@@ -43,6 +43,22 @@ class Report(ctypes.Structure):
     ]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device_bytes", c_int64), ("max_slots", c_int), ("max_iter", c_int), ("check_every", c_int),
+                ("tol", c_double), ("seed", c_uint64), ("inject_alloc_failures", c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("e0", c_double), ("iterations", c_int), ("converged", c_int), ("status", c_int),
+                ("latency_s", c_double), ("queue_s", c_double), ("run_s", c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("queued", c_int64),
+                ("running", c_int64), ("p50_s", c_double), ("p99_s", c_double), ("mean_s", c_double),
+                ("throughput_rps", c_double), ("device_bytes", c_int64), ("device_bytes_free", c_int64)]
+
+
 # (name, restype, argtypes) of every function declared in include/ed.h
 SIGNATURES = [
     ("ed_build_sectors", c_int, [P(ModelDesc), P(c_void_p)]),
@@ -52,6 +68,20 @@ SIGNATURES = [
     ("ed_lanczos_ground", c_int, [c_void_p, P(LanczosOpts), P(c_double), c_void_p, P(Report)]),
     ("ed_lanczos_gf", c_int, [c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_void_p, c_int, c_double,
                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("ed_batch_create", c_int, [c_void_p, c_int, c_int, P(c_void_p)]),
+    ("ed_batch_dim", c_int64, [c_void_p]),
+    ("ed_batch_offsets", c_int, [c_void_p, c_void_p]),
+    ("ed_batch_info", c_int, [c_void_p, c_void_p, c_void_p]),
+    ("ed_batch_apply", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    ("ed_batch_lanczos", c_int, [c_void_p, P(LanczosOpts), c_void_p, c_void_p, P(Report)]),
+    ("ed_batch_destroy", None, [c_void_p]),
+    ("ed_server_default_opts", None, [P(ServerOpts)]),
+    ("ed_server_create", c_int, [P(ServerOpts), P(c_void_p)]),
+    ("ed_server_submit", c_int, [c_void_p, P(ModelDesc), P(c_uint64)]),
+    ("ed_server_wait", c_int, [c_void_p, c_uint64, c_int, P(Result)]),
+    ("ed_server_cancel", c_int, [c_void_p, c_uint64]),
+    ("ed_server_get_stats", c_int, [c_void_p, P(ServerStats)]),
+    ("ed_server_destroy", None, [c_void_p]),
     ("ed_dim", c_int64, [c_void_p]),
     ("ed_num_blocks", c_int, [c_void_p]),
     ("ed_blocks", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -1,0 +1,507 @@
+// Class-sorted H|psi> (paper Eq. (2)) in three arithmetic flavours:
+//   FP32  storage and accumulation;
+//   FP64  storage and accumulation (models with non-dyadic couplings);
+//   I64   FP64 storage, exact 64-bit fixed-point accumulation: when every
+//         matrix element is an integer multiple of 2^-q_shift, x is scaled
+//         by one power of two per vector, summed exactly on the integer
+//         pipe and rounded once back to FP64.  FP64 adds and FP64
+//         conversions run at about 0.5 T/s on this GPU, the integer pipe at
+//         tens of T/s, so no FP64 instruction is issued per matrix element.
+// Row pass: psi_s[a,:] is staged in shared memory by bulk TMA copies
+// (double-buffered), then each column b sums, class by class, the H_B
+// neighbours (16-bit column indices) and the cross-cut gathers, plus the
+// diagonal.  Panel pass: the H_A (row-mixing) term over column panels that
+// stay resident in L2.
+#include <cstdint>
+#include <cstring>
+
+#include "ed_internal.h"
+
+namespace edk {
+
+struct P3 {
+  Dev3 t;
+  const DevBlock* blocks;
+  const DevCross* cross;
+  const long long* row_start;
+  int nblk;
+  int ncross;
+  long long n_rows;
+};
+
+struct PF32 {
+  using S = float;
+  __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
+  __device__ static float diag(const Dev3& t, long long gA, long long gB, unsigned z) {
+    float v = t.A_d32[gA] + t.B_d32[gB] + t.dc0_32;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
+    return v;
+  }
+};
+struct PF64 {
+  using S = double;
+  __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
+  __device__ static double diag(const Dev3& t, long long gA, long long gB, unsigned z) {
+    double v = t.A_d64[gA] + t.B_d64[gB] + t.dc0_64;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
+    return v;
+  }
+};
+struct PI64 {
+  using S = long long;
+  __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
+  __device__ static long long diag(const Dev3& t, long long gA, long long gB, unsigned z) {
+    long long v = (long long)t.A_dI[gA] + (long long)t.B_dI[gB] + t.dc0_I;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------- fixed point <-> FP64 by bit manipulation
+
+__host__ __device__ __forceinline__ unsigned long long f64_bits(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long u;
+  memcpy(&u, &v, 8);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double bits_f64(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  memcpy(&v, &u, 8);
+  return v;
+#endif
+}
+__host__ __device__ __forceinline__ int clz64(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)u);
+#else
+  return __builtin_clzll(u);
+#endif
+}
+
+// round(v * 2^sh_base) (ties away from zero) for |v| < 2^E, sh_base = P - E
+__host__ __device__ __forceinline__ long long to_fixed(double v, int sh_base) {
+  const unsigned long long u = f64_bits(v);
+  const int s = (int)(u >> 63);
+  int e = (int)((u >> 52) & 0x7ffull);
+  unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  if (e == 0) {
+    if (m == 0) return 0;
+    e = 1;
+  } else {
+    m |= 1ull << 52;
+  }
+  const int sh = e - 1075 + sh_base;
+  long long X;
+  if (sh >= 0) X = (long long)(m << sh);
+  else if (sh > -64) X = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else X = 0;
+  return s ? -X : X;
+}
+
+// Y * 2^e2 rounded to nearest (ties to even) FP64
+__host__ __device__ __forceinline__ double from_fixed(long long Y, int e2) {
+  if (Y == 0) return 0.0;
+  const unsigned long long s = Y < 0 ? 1ull : 0ull;
+  unsigned long long u = s ? (unsigned long long)(-Y) : (unsigned long long)Y;
+  int p = 63 - clz64(u);
+  unsigned long long mant;
+  if (p <= 52) {
+    mant = u << (52 - p);
+  } else {
+    const int sh = p - 52;
+    mant = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1);
+    const unsigned long long half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++p;
+      }
+    }
+  }
+  const int ex = p + e2 + 1023;
+  if (ex <= 0) return s ? -0.0 : 0.0;
+  if (ex >= 2047) return bits_f64((s << 63) | (0x7ffull << 52));
+  return bits_f64((s << 63) | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull));
+}
+
+// host entry points of the two conversions (used by the CPU tests)
+long long host_to_fixed(double v, int sh_base) { return to_fixed(v, sh_base); }
+double host_from_fixed(long long Y, int e2) { return from_fixed(Y, e2); }
+
+// largest biased exponent of x (atomic max into out[0]; out must start at 0)
+__global__ void k_exp_max(const double* __restrict__ x, long long n, int* out) {
+  int m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, (int)(((unsigned long long)__double_as_longlong(x[i]) >> 52) & 0x7ffull));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// |x| < 2^E with E = emax - 1022; X = round(x * 2^(P - E))
+__global__ void k_to_fixed(const double* __restrict__ x, long long* __restrict__ X, long long n,
+                           const int* __restrict__ emax, int P) {
+  const int E = emax[0] - 1022;
+  const int sh = P - E;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    X[i] = to_fixed(x[i], sh);
+}
+
+__device__ __forceinline__ int out_exp(const Dev3& t, const int* emax) { return (emax[0] - 1022) - t.P - t.q_shift; }
+
+template <class Pol>
+__device__ __forceinline__ void store_out(typename Pol::S* y, long long i, typename Pol::S v, bool final_,
+                                          int e2) {
+  y[i] = v;
+}
+template <>
+__device__ __forceinline__ void store_out<PI64>(long long* y, long long i, long long v, bool final_, int e2) {
+  if (final_) reinterpret_cast<double*>(y)[i] = from_fixed(v, e2);
+  else y[i] = v;
+}
+
+// ---------------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ unsigned s_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   s_u32(dst)),
+               "l"(src), "r"(bytes), "r"(s_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long i = 0; i < (1ll << 22); ++i) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(s_u32(bar)), "r"(parity)
+                 : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int find_blk(const long long* row_start, int nblk, long long row) {
+  int lo = 0, hi = nblk - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (row_start[mid] <= row) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kRowThreads = 512;
+
+// Row pass: work unit = R consecutive rows of one block ("row group").  The
+// rows are brought into shared memory by bulk TMA copies; two CTAs share an
+// SM so that one CTA's copy overlaps the other's compute.  Per column b the
+// class-sorted CSR indices of H_B are read once and gathered from all R
+// rows; index loads are issued four at a time.
+template <class Pol, int R>
+__global__ void __launch_bounds__(kRowThreads, 2)
+    k_row4(P3 p, const long long* __restrict__ grp_start, long long n_groups, const typename Pol::S* __restrict__ x,
+           typename Pol::S* __restrict__ y, const int* __restrict__ emax, long long stage_elems, int* err) {
+  using S = typename Pol::S;
+  extern __shared__ __align__(16) unsigned char smem4[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem4);
+  S* bufs = reinterpret_cast<S*>(smem4 + 128);
+  __shared__ const S* src_row[R][32];
+  __shared__ int src_ib[32];
+  __shared__ int s_pad[R];
+  constexpr int V = 16 / (int)sizeof(S);
+  const Dev3& t = p.t;
+  if (threadIdx.x == 0) {
+    bar_init(&bar[0]);
+    bar_fence_init();
+  }
+  __syncthreads();
+  const int e2 = emax ? out_exp(t, emax) : 0;
+  unsigned phase = 0;
+  for (long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+    const int bi = find_blk(grp_start, p.nblk, g);
+    const DevBlock bl = p.blocks[bi];
+    const long long a0 = (g - grp_start[bi]) * R;
+    const int nr = (int)min((long long)R, bl.dA - a0);
+    const long long dB = bl.dB;
+    // start the bulk copies of the group's rows
+    if (threadIdx.x == 0) {
+      proxy_fence();
+      unsigned bytes = 0;
+      for (int r = 0; r < nr; ++r) {
+        const long long g0 = bl.off + (a0 + r) * dB;
+        const long long gal = (g0 + V - 1) / V * V, galend = (g0 + dB) / V * V;
+        if (galend > gal) bytes += (unsigned)((galend - gal) * (long long)sizeof(S));
+      }
+      if (bytes) {
+        bar_expect(&bar[0], bytes);
+        for (int r = 0; r < nr; ++r) {
+          const long long g0 = bl.off + (a0 + r) * dB;
+          const long long gal = (g0 + V - 1) / V * V, galend = (g0 + dB) / V * V;
+          if (galend > gal)
+            bulk_g2s(bufs + r * stage_elems + (g0 % V) + (gal - g0), x + gal,
+                     (unsigned)((galend - gal) * (long long)sizeof(S)), &bar[0]);
+        }
+      } else {
+        bar_arrive(&bar[0]);
+      }
+    }
+    // ragged ends of each row, plain loads
+    for (int r = 0; r < nr; ++r) {
+      const long long g0 = bl.off + (a0 + r) * dB;
+      const long long gend = g0 + dB;
+      const long long gal = (g0 + V - 1) / V * V, galend = gend / V * V;
+      const int pad = (int)(g0 % V);
+      S* buf = bufs + r * stage_elems;
+      if (threadIdx.x == 0) s_pad[r] = pad;
+      if (galend > gal) {
+        for (long long q = g0 + threadIdx.x; q < gal; q += blockDim.x) buf[pad + (q - g0)] = x[q];
+        for (long long q = galend + threadIdx.x; q < gend; q += blockDim.x) buf[pad + (q - g0)] = x[q];
+      } else {
+        for (long long q = g0 + threadIdx.x; q < gend; q += blockDim.x) buf[pad + (q - g0)] = x[q];
+      }
+    }
+    // cross-cut source rows, one per (row, cross bond)
+    if (threadIdx.x < 32 * R) {
+      const int r = threadIdx.x >> 5, k = threadIdx.x & 31;
+      const S* sp = nullptr;
+      if (r < nr && k < p.ncross) {
+        const long long gA = bl.gA0 + a0 + r;
+        const unsigned pa = t.A_pack[gA];
+        const DevCross cr = p.cross[k];
+        const int sb = ((pa >> k) & 1u) ? bl.nbr_lo : bl.nbr_hi;
+        if (sb >= 0) {
+          const DevBlock so = p.blocks[sb];
+          const unsigned rr = t.mapA[(long long)cr.ia * t.A_total + gA];
+          if (rr != 0xFFFFu) sp = x + so.off + (long long)rr * so.dB;
+        }
+        if (r == 0) src_ib[k] = cr.ib;
+      }
+      src_row[r][k] = sp;
+    }
+    const bool ok = bar_wait(&bar[0], phase);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      bar_wait(&bar[0], phase);
+      return;
+    }
+    phase ^= 1;
+    unsigned pa[R];
+    const S* xs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int rr = r < nr ? r : 0;
+      pa[r] = t.A_pack[bl.gA0 + a0 + rr];
+      xs[r] = bufs + rr * stage_elems + s_pad[rr];
+    }
+    const bool final_ = !bl.has_hA;
+    for (long long b = threadIdx.x; b < dB; b += blockDim.x) {
+      const long long gB = bl.gB0 + b;
+      const uint2 m = t.B_meta[gB];
+      const unsigned pb = t.B_pack[gB];
+      S acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const unsigned z = t.vab_and ? (pa[r] & pb) : (pa[r] ^ pb);
+        acc[r] = Pol::diag(t, bl.gA0 + a0 + (r < nr ? r : 0), gB, z) * xs[r][b];
+      }
+      unsigned e = m.x;
+#pragma unroll
+      for (int c = 0; c < kMaxCls; ++c) {
+        const unsigned n = (m.y >> (8 * c)) & 255u;
+        if (!n) continue;
+        S sum[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) sum[r] = 0;
+        unsigned i = 0;
+        for (; i + 4 <= n; i += 4) {
+          const unsigned c0 = t.B_col[e + i], c1 = t.B_col[e + i + 1], c2 = t.B_col[e + i + 2], c3 = t.B_col[e + i + 3];
+#pragma unroll
+          for (int r = 0; r < R; ++r) sum[r] += (xs[r][c0] + xs[r][c1]) + (xs[r][c2] + xs[r][c3]);
+        }
+        for (; i < n; ++i) {
+          const unsigned c0 = t.B_col[e + i];
+#pragma unroll
+          for (int r = 0; r < R; ++r) sum[r] += xs[r][c0];
+        }
+        e += n;
+        const S wc = Pol::w(t, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += wc * sum[r];
+      }
+      if (p.ncross) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r >= nr) break;
+          const unsigned diff = pa[r] ^ pb;
+#pragma unroll
+          for (int c = 0; c < kMaxCls; ++c) {
+            unsigned dd = diff & t.cross_cls_mask[c];
+            if (!dd) continue;
+            S sum = 0;
+            while (dd) {
+              const int k = __ffs(dd) - 1;
+              dd &= dd - 1;
+              const S* sp = src_row[r][k];
+              if (sp) sum += __ldg(sp + t.mapB[(long long)src_ib[k] * t.B_total + gB]);
+            }
+            acc[r] += Pol::w(t, c) * sum;
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r < nr) store_out<Pol>(y, bl.off + (a0 + r) * dB + b, acc[r], final_, e2);
+    }
+    __syncthreads();
+  }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256) k_panel3(P3 p, const int4* __restrict__ items, long long n_items,
+                                                const typename Pol::S* __restrict__ x, typename Pol::S* __restrict__ y,
+                                                const int* __restrict__ emax) {
+  using S = typename Pol::S;
+  constexpr int NC = 8;  // columns per lane: panels of 256 columns
+  const Dev3& t = p.t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e2 = emax ? out_exp(t, emax) : 0;
+  for (long long w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int4 it = items[w];
+    if (warp >= it.w) continue;
+    const DevBlock bl = p.blocks[it.x];
+    const long long a = it.z + warp;
+    const long long gA = bl.gA0 + a;
+    const long long dB = bl.dB;
+    const S* xb = x + bl.off;
+    S* yrow = y + bl.off + a * dB;
+    S acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const long long b = it.y + lane + 32 * c;
+      acc[c] = b < dB ? yrow[b] : (S)0;
+    }
+    const uint2 m = t.A_meta[gA];
+    unsigned e = m.x;
+#pragma unroll
+    for (int cl = 0; cl < kMaxCls; ++cl) {
+      const unsigned n = (m.y >> (8 * cl)) & 255u;
+      if (!n) continue;
+      S sum[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) sum[c] = 0;
+      for (unsigned i = 0; i < n; ++i) {
+        const S* xr = xb + (long long)t.A_col[e + i] * dB;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const long long b = it.y + lane + 32 * c;
+          if (b < dB) sum[c] += __ldg(xr + b);
+        }
+      }
+      e += n;
+      const S wc = Pol::w(t, cl);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += wc * sum[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const long long b = it.y + lane + 32 * c;
+      if (b < dB) store_out<Pol>(yrow, b, acc[c], true, e2);
+    }
+  }
+}
+
+static int n_sms(int dev) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    n = 148;
+  }
+  return n;
+}
+
+static P3 make_p3(const ed_ctx* c) {
+  P3 p;
+  p.t = c->t3;
+  p.blocks = c->d_blocks;
+  p.cross = c->d_cross;
+  p.row_start = c->d_row_start;
+  p.nblk = (int)c->blocks.size();
+  p.ncross = c->kind == ED_SPIN ? (int)c->cross.size() : 0;
+  p.n_rows = c->n_rows;
+  return p;
+}
+
+// rows per CTA pass: two for 4-byte types, one for 8-byte types
+static int rows_per_pass(size_t es) { return es == 4 ? 2 : 1; }
+
+static size_t v3_smem(const ed_ctx* c, size_t es, long long* stage_elems) {
+  long long mdb = 1;
+  for (const auto& b : c->blocks) mdb = std::max<long long>(mdb, b.dB);
+  *stage_elems = ((mdb + 16 / (long long)es + 15) / 16) * 16;
+  return 128 + (size_t)rows_per_pass(es) * (size_t)(*stage_elems) * es;
+}
+
+bool v3_usable(const ed_ctx* c, ed_dtype dt, const void* x) {
+  if (!c->v3_ok || ((uintptr_t)x % 16) != 0) return false;
+  long long se;
+  return v3_smem(c, dt == ED_F64 ? 8 : 4, &se) <= 110 * 1024;
+}
+
+template <class Pol>
+static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y, const int* emax, cudaStream_t st) {
+  P3 p = make_p3(c);
+  if (p.n_rows == 0) return ED_OK;
+  long long se;
+  constexpr int R = sizeof(typename Pol::S) == 4 ? 2 : 1;
+  const size_t smem = v3_smem(c, sizeof(typename Pol::S), &se);
+  auto kern = k_row4<Pol, R>;
+  ED_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int sms = n_sms(c->device);
+  const long long* gs = R == 2 ? c->d_grp2_start : c->d_row_start;
+  const long long ng = R == 2 ? c->n_grp2 : c->n_rows;
+  const long long grid = std::min<long long>(ng, (long long)sms * 2);
+  kern<<<(unsigned)grid, kRowThreads, smem, st>>>(p, gs, ng, x, y, emax, se, c->d_err);
+  ED_CUDA_TRY(cudaGetLastError());
+  if (c->n_panel_items > 0) {
+    const long long g2 = std::min<long long>(c->n_panel_items, (long long)sms * 8);
+    k_panel3<Pol><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
+    ED_CUDA_TRY(cudaGetLastError());
+  }
+  return ED_OK;
+}
+
+ed_status apply_v3(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t st) {
+  if (dt == ED_F32) return run_v3<PF32>(c, (const float*)x, (float*)y, nullptr, st);
+  if (!c->dyadic) return run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st);
+  // exact fixed point: exponent of max|x|, scaled copy, integer passes
+  if (!c->d_fixed) ED_TRY(dev_alloc(c, (void**)&c->d_fixed, (size_t)std::max<long long>(c->D, 2) * 8));
+  const long long n = c->D;
+  ED_CUDA_TRY(cudaMemsetAsync(c->d_exp, 0, sizeof(int), st));
+  const int sms = n_sms(c->device);
+  const long long g = std::min<long long>((n + 255) / 256, (long long)sms * 8);
+  k_exp_max<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>((const double*)x, n, c->d_exp);
+  k_to_fixed<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>((const double*)x, c->d_fixed, n, c->d_exp, c->t3.P);
+  ED_CUDA_TRY(cudaGetLastError());
+  return run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st);
+}
+
+}  // namespace edk

@@ -45,6 +45,9 @@ struct DevBuf {
 
 enum BasisKind { BASIS_NONE = 0, BASIS_SAME = 1, BASIS_BF16 = 2 };
 
+// relative Ritz-residual target when an eigenvector is returned
+constexpr double kVecResid = 1e-10;
+
 // Lanczos basis kept on the device as one contiguous array of `cap`
 // vectors (same type as the recurrence, or BF16 when only a restart vector
 // is needed).  When it does not fit the budget the vectors are recomputed
@@ -105,9 +108,11 @@ struct RunOut {
 };
 
 // Three-term Lanczos recurrence from the normalised v0 (device, type T).
+// resid_tol > 0 additionally requires the Ritz residual estimate
+// beta_m |s_m| <= resid_tol (used when an eigenvector is wanted).
 template <typename T>
 ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_iter, double tol, int check_every,
-                 bool fixed, bool reorth, Basis* basis, RunOut& out) {
+                 bool fixed, bool reorth, Basis* basis, RunOut& out, double resid_tol = 0.0) {
   const long long n = c->D;
   T* vprev = bufs[0];
   T* v = bufs[1];
@@ -139,7 +144,13 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
     const bool breakdown = ab[1] <= 1e-13 * (scale > 0 ? scale : 1.0);
     if (!fixed && (m % check_every == 0 || breakdown)) {
       double th = tridiag_lowest(out.alpha.data(), out.beta.data(), m);
-      if (std::fabs(th - theta_prev) <= tol * std::fabs(th)) {
+      bool ok = std::fabs(th - theta_prev) <= tol * std::fabs(th);
+      if (ok && resid_tol > 0.0 && !breakdown) {
+        std::vector<double> sv;
+        tridiag_vector(out.alpha.data(), out.beta.data(), m, th, sv);
+        ok = std::fabs(ab[1] * sv[m - 1]) <= resid_tol * std::max(1.0, std::fabs(th));
+      }
+      if (ok) {
         out.converged = true;
         break;
       }
@@ -292,7 +303,8 @@ extern "C" ed_status ed_lanczos_ground(ed_ctx* c, const ed_lanczos_opts* opts_in
     Basis B;
     if (o.reorth || want_vec) B.init(BASIS_SAME, sizeof(double), n, max_iter + 1, budget);
     RunOut r;
-    ED_TRY(lz_run<double>(c, st, bufs, v0, max_iter, o.tol, o.check_every, o.fixed_iter != 0, o.reorth != 0, &B, r));
+    ED_TRY(lz_run<double>(c, st, bufs, v0, max_iter, o.tol, o.check_every, o.fixed_iter != 0, o.reorth != 0, &B, r,
+                          want_vec ? kVecResid : 0.0));
     record_ab(r);
     R.iterations = (int)r.alpha.size();
     energy = r.theta;
@@ -344,7 +356,8 @@ extern "C" ed_status ed_lanczos_ground(ed_ctx* c, const ed_lanczos_opts* opts_in
         Basis B64;
         if (want_vec) B64.init(BASIS_SAME, sizeof(double), n, blk + 1, free_device_bytes() / 2);
         RunOut r2;
-        ED_TRY(lz_run<double>(c, st, bufs, x, blk, o.tol, o.check_every, false, false, &B64, r2));
+        ED_TRY(lz_run<double>(c, st, bufs, x, blk, o.tol, o.check_every, false, false, &B64, r2,
+                              want_vec ? kVecResid : 0.0));
         R.iterations += (int)r2.alpha.size();
         R.restarts += 1;
         energy = r2.theta;

@@ -73,6 +73,8 @@ struct DevBlock {
   int s, kB;
   int nbr_lo, nbr_hi;   // block index of charge s-1 / s+1 (-1 if absent)
   long long dA, dB, off, gA0, gB0, row0;
+  int has_hA;           // the block's rows have H_A entries (second pass needed)
+  int pad_;
 };
 
 struct DevCross {
@@ -104,6 +106,47 @@ struct DevTables {
   const unsigned long long* A_key;  // bit-string key part of each side state
   const unsigned long long* B_key;  //   (key = A_key | B_key)
   long long A_total, B_total;
+};
+
+// Tables of the class-sorted apply path.  Off-diagonal matrix elements take
+// at most kMaxCls distinct values ("classes"); each CSR row lists its
+// columns grouped by class (16-bit indices), so no value is stored per
+// entry.  When every coupling is a dyadic rational (value * 2^q_shift is a
+// small integer) the FP64 apply runs in exact 64-bit fixed point.
+constexpr int kMaxCls = 4;
+
+struct Dev3 {
+  const uint2* A_meta;      // x: first entry, y: per-class counts (8 bits each)
+  const uint16_t* A_col;
+  const uint2* B_meta;
+  const uint16_t* B_col;
+  const uint32_t* A_pack;   // packed cross-bond bits (spin) or up string (Hubbard)
+  const uint32_t* B_pack;
+  const float* A_d32;
+  const float* B_d32;
+  const double* A_d64;
+  const double* B_d64;
+  const int* A_dI;          // side diagonal in units of 2^-q_shift
+  const int* B_dI;
+  const uint16_t* mapA;     // [n_cross_A_bits][A_total]
+  const uint16_t* mapB;     // [n_cross_B_bits][B_total]
+  long long A_total, B_total;
+  float w32[kMaxCls];
+  double w64[kMaxCls];
+  long long wI[kMaxCls];
+  // diagonal cross term: c0 + sum_c dw_c popc(f(pa,pb) & dmask_c)
+  int vab_and;
+  int ncls_d;
+  unsigned dmask[kMaxClasses];
+  float dw32[kMaxClasses];
+  double dw64[kMaxClasses];
+  long long dwI[kMaxClasses];
+  float dc0_32;
+  double dc0_64;
+  long long dc0_I;
+  unsigned cross_cls_mask[kMaxCls];  // cross bonds (bit k) with off-diagonal class c
+  int q_shift;              // values * 2^q_shift are integers (fixed-point path)
+  int P;                    // fraction bits of the fixed-point vector
 };
 
 struct DevDiagParams {
@@ -151,6 +194,18 @@ struct ed_ctx {
   std::vector<edk::DevBlock> h_blocks;
   std::vector<edk::DevCross> h_cross;
   long long* d_row_start = nullptr;  // per block first row (for row -> block lookup)
+  int4* d_panel_items = nullptr;     // (block, first column, first row, rows) of the H_A pass
+  long long* d_grp2_start = nullptr; // per block: first two-row group (plus total)
+  long long n_grp2 = 0;
+  long long n_panel_items = 0;
+  int* d_err = nullptr;              // set by kernels whose bounded waits ran out
+  // class-sorted path
+  bool v3_ok = false;                // tables below are valid
+  bool dyadic = false;               // FP64 apply may use exact fixed point
+  edk::Dev3 t3{};
+  long long* d_fixed = nullptr;      // fixed-point copy of x (lazily allocated, D entries)
+  int* d_exp = nullptr;              // exponent scratch of the fixed-point path
+  std::vector<int> cross_cls;        // class of each cross bond
   // per-side CSR stats
   int64_t nnzA = 0, nnzB = 0;
   // Lanczos / GF work buffers (lazily allocated)
@@ -162,6 +217,16 @@ struct ed_ctx {
 };
 
 namespace edk {
+// host copy of one side's operators (CSR over the side's global state index)
+struct HostSideOps {
+  std::vector<int> rowptr, col;
+  std::vector<double> val64, diag;
+  std::vector<float> val32;
+  std::vector<unsigned long long> pack;
+  std::vector<int> maps;  // [n_cross_bits][total]
+};
+ed_status build_side_ops(const ed_ctx* c, const Side& sd, const std::vector<ed_ctx::SideBond>& bonds, bool sideA,
+                         HostSideOps& h);
 ed_status dev_alloc(ed_ctx* c, void** p, size_t bytes);
 template <typename T>
 ed_status upload(ed_ctx* c, T** dptr, const std::vector<T>& h) {

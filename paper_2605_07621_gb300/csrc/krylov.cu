@@ -11,61 +11,13 @@
 
 #include "ed_internal.h"
 #include "krylov.h"
+#include "reduce.cuh"
 
 namespace edk {
 
 constexpr int kRedThreads = 256;
 
 // ---------------------------------------------------------------- reductions
-
-// float-float accumulation (Dekker 1971 / Knuth TwoSum + FMA TwoProd)
-struct FAcc {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float a) {
-    float s = hi + a;
-    float bp = s - hi;
-    float err = (hi - (s - bp)) + (a - bp);
-    hi = s;
-    lo += err;
-  }
-  __device__ __forceinline__ void add_prod(float x, float y) {
-    float p = x * y;
-    float e = fmaf(x, y, -p);
-    add(p);
-    lo += e;
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
-template <typename T>
-struct DotAcc;
-template <>
-struct DotAcc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add_prod(double x, double y) { s = fma(x, y, s); }
-  __device__ __forceinline__ double value() const { return s; }
-};
-template <>
-struct DotAcc<float> {
-  FAcc f;
-  __device__ __forceinline__ void add_prod(float x, float y) { f.add_prod(x, y); }
-  __device__ __forceinline__ double value() const { return f.value(); }
-};
-
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double red[kRedThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    s = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
-  return s;  // valid in thread 0
-}
 
 // sum of partials in fixed order -> out[0]; op 1: sqrt of the sum
 __global__ void k_finalize(const double* __restrict__ part, int n, double* out, int op) {

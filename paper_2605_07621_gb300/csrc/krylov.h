@@ -12,7 +12,7 @@ namespace edk {
 constexpr int kMaxPartials = 4096;
 constexpr int kMaxBasis = 2048;  // reorthogonalisation coefficients kept on the device
 
-ed_status apply_H_impl(const ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t st);
+ed_status apply_H_impl(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t st);
 ed_status random_vector_impl(const ed_ctx* c, uint64_t seed, void* x, ed_dtype dt, cudaStream_t st);
 
 int grid_for(const ed_ctx* c, long long n);

@@ -9,6 +9,7 @@
 //   * the cross-cut maps: for every A site p touched by a cross bond, the
 //     rank of a XOR (1<<p) in its new charge sector (likewise for B), i.e.
 //     the partial permutations L_m, R_m of Eq. (2) in index form.
+#include <cmath>
 #include <cstring>
 
 #include "ed_internal.h"
@@ -17,14 +18,6 @@ using namespace edk;
 
 namespace {
 
-struct HostSideOps {
-  std::vector<int> rowptr, col;
-  std::vector<double> val64, diag;
-  std::vector<float> val32;
-  std::vector<unsigned long long> pack;
-  std::vector<int> maps;  // [n_cross_bits][total]
-};
-
 inline int parity_between(uint32_t x, int p, int q) {
   int lo = p < q ? p : q, hi = p < q ? q : p;
   if (hi - lo <= 1) return 0;
@@ -32,6 +25,9 @@ inline int parity_between(uint32_t x, int p, int q) {
   return __builtin_popcount(x & m) & 1;
 }
 
+}  // namespace
+
+namespace edk {
 ed_status build_side_ops(const ed_ctx* c, const Side& sd, const std::vector<ed_ctx::SideBond>& bonds, bool sideA,
                          HostSideOps& h) {
   const bool hub = c->kind == ED_HUBBARD;
@@ -99,8 +95,160 @@ ed_status build_side_ops(const ed_ctx* c, const Side& sd, const std::vector<ed_c
   }
   return ED_OK;
 }
+}  // namespace edk
+
+namespace {
+
+// exact test: v * 2^k is an integer of magnitude <= 2^24
+bool dyadic_at(double v, int k) {
+  double t = std::ldexp(v, k);
+  return std::fabs(t) <= 16777216.0 && t == std::trunc(t);
+}
+
+struct Side3 {
+  std::vector<uint2> meta;
+  std::vector<uint16_t> col;
+  std::vector<uint32_t> pack;
+  std::vector<int> dI;
+};
+
+// class-sorted copy of one side's CSR
+bool build_side3(const HostSideOps& h, const std::vector<double>& cls_val, Side3& o) {
+  const int64_t tot = (int64_t)h.rowptr.size() - 1;
+  o.meta.resize(tot);
+  o.col.clear();
+  o.col.reserve(h.col.size());
+  for (int64_t g = 0; g < tot; ++g) {
+    uint32_t cnt[kMaxCls] = {0, 0, 0, 0};
+    const uint32_t start = (uint32_t)o.col.size();
+    for (int c = 0; c < (int)cls_val.size(); ++c) {
+      for (int e = h.rowptr[g]; e < h.rowptr[g + 1]; ++e) {
+        if (h.val64[e] != cls_val[c]) continue;
+        if (h.col[e] > 0xFFFF) return false;
+        o.col.push_back((uint16_t)h.col[e]);
+        ++cnt[c];
+      }
+      if (cnt[c] > 255) return false;
+    }
+    o.meta[g] = make_uint2(start, cnt[0] | (cnt[1] << 8) | (cnt[2] << 16) | (cnt[3] << 24));
+  }
+  o.pack.resize(tot);
+  for (int64_t g = 0; g < tot; ++g) o.pack[g] = (uint32_t)h.pack[g];
+  return true;
+}
 
 }  // namespace
+
+// Tables of the class-sorted path; leaves c->v3_ok false when the model
+// needs more than kMaxCls off-diagonal values, more than 32 cross bonds or
+// sides with more than 65535 states per charge.
+static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& hb) {
+  c->v3_ok = false;
+  c->dyadic = false;
+  if (c->cross.size() > 32) return ED_OK;
+  if (c->kind == ED_HUBBARD && c->n_sites > 32) return ED_OK;
+  for (const Block& b : c->blocks)
+    if (b.dA > 65535 || b.dB > 65535) return ED_OK;
+  std::vector<double> cls;
+  auto add_cls = [&](double v) {
+    if (std::find(cls.begin(), cls.end(), v) == cls.end()) cls.push_back(v);
+  };
+  for (double v : ha.val64) add_cls(v);
+  for (double v : hb.val64) add_cls(v);
+  for (const auto& cb : c->cross) add_cls(cb.coef);
+  if (cls.size() > (size_t)kMaxCls) return ED_OK;
+  Side3 a3, b3;
+  if (!build_side3(ha, cls, a3) || !build_side3(hb, cls, b3)) return ED_OK;
+  Dev3& t = c->t3;
+  t = Dev3{};
+  for (size_t i = 0; i < cls.size(); ++i) {
+    t.w64[i] = cls[i];
+    t.w32[i] = (float)cls[i];
+  }
+  c->cross_cls.assign(c->cross.size(), 0);
+  for (size_t k = 0; k < c->cross.size(); ++k) {
+    int ci = (int)(std::find(cls.begin(), cls.end(), c->cross[k].coef) - cls.begin());
+    c->cross_cls[k] = ci;
+    t.cross_cls_mask[ci] |= 1u << k;
+  }
+  const DevDiagParams& dp = c->diag;
+  t.vab_and = dp.vab_and;
+  t.ncls_d = dp.ncls;
+  for (int q = 0; q < dp.ncls; ++q) {
+    if (dp.mask[q] >> 32) return ED_OK;
+    t.dmask[q] = (unsigned)dp.mask[q];
+    t.dw64[q] = dp.w[q];
+    t.dw32[q] = (float)dp.w[q];
+  }
+  t.dc0_64 = dp.c0;
+  t.dc0_32 = (float)dp.c0;
+  // dyadic scale for the exact fixed-point FP64 path
+  std::vector<double> vals(cls.begin(), cls.end());
+  vals.push_back(dp.c0);
+  for (int q = 0; q < dp.ncls; ++q) vals.push_back(dp.w[q]);
+  int qs = -1;
+  for (int k = 0; k <= 30 && qs < 0; ++k) {
+    bool ok = true;
+    for (double v : vals) ok = ok && dyadic_at(v, k);
+    for (size_t g = 0; ok && g < ha.diag.size(); ++g) ok = dyadic_at(ha.diag[g], k);
+    for (size_t g = 0; ok && g < hb.diag.size(); ++g) ok = dyadic_at(hb.diag[g], k);
+    if (ok) qs = k;
+  }
+  if (qs >= 0) {
+    t.q_shift = qs;
+    for (size_t i = 0; i < cls.size(); ++i) t.wI[i] = (long long)std::ldexp(cls[i], qs);
+    for (int q = 0; q < dp.ncls; ++q) t.dwI[q] = (long long)std::ldexp(dp.w[q], qs);
+    t.dc0_I = (long long)std::ldexp(dp.c0, qs);
+    a3.dI.resize(ha.diag.size());
+    b3.dI.resize(hb.diag.size());
+    for (size_t g = 0; g < ha.diag.size(); ++g) a3.dI[g] = (int)std::ldexp(ha.diag[g], qs);
+    for (size_t g = 0; g < hb.diag.size(); ++g) b3.dI[g] = (int)std::ldexp(hb.diag[g], qs);
+    // bound on sum_j |M_ij| (units 2^-q_shift) -> headroom of the int64 sums
+    auto side_max = [&](const Side3& s3, const std::vector<int>& dI) {
+      double m = 0.0;
+      for (size_t g = 0; g < s3.meta.size(); ++g) {
+        double r = std::fabs((double)dI[g]);
+        for (int cc = 0; cc < kMaxCls; ++cc) r += ((s3.meta[g].y >> (8 * cc)) & 255u) * std::fabs((double)t.wI[cc]);
+        m = std::max(m, r);
+      }
+      return m;
+    };
+    double rmax = side_max(a3, a3.dI) + side_max(b3, b3.dI) + std::fabs((double)t.dc0_I);
+    for (int q = 0; q < dp.ncls; ++q) rmax += std::fabs((double)t.dwI[q]) * __builtin_popcountll(dp.mask[q]);
+    for (size_t k = 0; k < c->cross.size(); ++k) rmax += std::fabs((double)t.wI[c->cross_cls[k]]);
+    int bits = (int)std::ceil(std::log2(rmax + 1.0));
+    t.P = std::min(60, 62 - bits);
+    c->dyadic = t.P >= 40;
+  }
+  // upload
+  uint2 *Am, *Bm;
+  uint16_t *Ac, *Bc, *mA, *mB;
+  uint32_t *Ap, *Bp;
+  int *AdI = nullptr, *BdI = nullptr;
+  ED_TRY(upload(c, &Am, a3.meta));
+  ED_TRY(upload(c, &Bm, b3.meta));
+  ED_TRY(upload(c, &Ac, a3.col));
+  ED_TRY(upload(c, &Bc, b3.col));
+  ED_TRY(upload(c, &Ap, a3.pack));
+  ED_TRY(upload(c, &Bp, b3.pack));
+  if (c->dyadic) {
+    ED_TRY(upload(c, &AdI, a3.dI));
+    ED_TRY(upload(c, &BdI, b3.dI));
+  }
+  std::vector<uint16_t> ma(ha.maps.size()), mb(hb.maps.size());
+  for (size_t i = 0; i < ma.size(); ++i) ma[i] = ha.maps[i] < 0 ? 0xFFFF : (uint16_t)ha.maps[i];
+  for (size_t i = 0; i < mb.size(); ++i) mb[i] = hb.maps[i] < 0 ? 0xFFFF : (uint16_t)hb.maps[i];
+  ED_TRY(upload(c, &mA, ma));
+  ED_TRY(upload(c, &mB, mb));
+  t.A_meta = Am; t.B_meta = Bm; t.A_col = Ac; t.B_col = Bc; t.A_pack = Ap; t.B_pack = Bp;
+  t.A_dI = AdI; t.B_dI = BdI; t.mapA = mA; t.mapB = mB;
+  t.A_d32 = c->tab.A_diag32; t.B_d32 = c->tab.B_diag32; t.A_d64 = c->tab.A_diag; t.B_d64 = c->tab.B_diag;
+  t.A_total = c->A.total();
+  t.B_total = c->B.total();
+  ED_TRY(dev_alloc(c, (void**)&c->d_exp, 64));
+  c->v3_ok = true;
+  return ED_OK;
+}
 
 extern "C" ed_status ed_build_local_ops(ed_ctx* c, int flags) {
   if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }
@@ -162,15 +310,48 @@ extern "C" ed_status ed_build_local_ops(ed_ctx* c, int flags) {
     db.nbr_lo = (b.s - 1 >= 0) ? c->block_of_s[b.s - 1] : -1;
     db.nbr_hi = (b.s + 1 < (int)c->block_of_s.size()) ? c->block_of_s[b.s + 1] : -1;
     db.dA = b.dA; db.dB = b.dB; db.off = b.off; db.gA0 = b.gA0; db.gB0 = b.gB0; db.row0 = b.row0;
+    db.has_hA = ha.rowptr[c->A.start[b.s] + b.dA] != ha.rowptr[c->A.start[b.s]] ? 1 : 0;
+    db.pad_ = 0;
     c->h_blocks.push_back(db);
     rs.push_back(b.row0);
   }
   rs.push_back(c->n_rows);
   ED_TRY(upload(c, &c->d_blocks, c->h_blocks));
   ED_TRY(upload(c, &c->d_row_start, rs));
+  {
+    std::vector<long long> g2;
+    long long acc = 0;
+    for (const Block& b : c->blocks) {
+      g2.push_back(acc);
+      acc += (b.dA + 1) / 2;
+    }
+    g2.push_back(acc);
+    c->n_grp2 = acc;
+    ED_TRY(upload(c, &c->d_grp2_start, g2));
+  }
   c->h_cross.clear();
   for (const auto& cb : c->cross) c->h_cross.push_back(DevCross{cb.ia, cb.ib, cb.coef});
   ED_TRY(upload(c, &c->d_cross, c->h_cross));
+  // H_A work items: block by block, column panel by column panel, 8 rows each
+  {
+    std::vector<int4> items;
+    const int panel_cols = 256, panel_rows = 8;
+    for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+      const Block& b = c->blocks[bi];
+      const int64_t r0 = c->A.start[b.s];
+      if (ha.rowptr[r0 + b.dA] == ha.rowptr[r0]) continue;  // no H_A entries in this sector
+      for (int64_t col = 0; col < b.dB; col += panel_cols)
+        for (int64_t a = 0; a < b.dA; a += panel_rows)
+          items.push_back(make_int4((int)bi, (int)col, (int)a, (int)std::min<int64_t>(panel_rows, b.dA - a)));
+    }
+    c->n_panel_items = (long long)items.size();
+    ED_TRY(upload(c, &c->d_panel_items, items));
+  }
+  {
+    std::vector<int> z(4, 0);
+    ED_TRY(upload(c, &c->d_err, z));
+  }
+  ED_TRY(build_v3(c, ha, hb));
   c->ops_flags = flags;
   c->ops_built = true;
   return ED_OK;

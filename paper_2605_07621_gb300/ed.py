@@ -232,3 +232,133 @@ def lanczos_gf(ctx: Context, psi0, e0: float, omega, eta: float, site: int = 0, 
                                    ctypes.addressof(wh), _stream_handle(stream)))
     coeffs = {"particle": (wp.value, ap, bp), "hole": (wh.value, ah, bh)}
     return G[0::2] + 1j * G[1::2], coeffs
+
+
+class Batch:
+    """Owns an ``ed_batch*`` (batched independent instances)."""
+
+    def __init__(self, handle: int, models):
+        self._h = ctypes.c_void_p(handle)
+        self.models = models
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            L.load().ed_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dim(self) -> int:
+        return int(L.load().ed_batch_dim(self._h))
+
+    def offsets(self) -> np.ndarray:
+        off = np.zeros(len(self.models) + 1, np.int64)
+        L.check(L.load().ed_batch_offsets(self._h, off.ctypes.data))
+        return off
+
+    def info(self):
+        thr = ctypes.c_int()
+        ms = np.zeros(5, np.float32)
+        L.check(L.load().ed_batch_info(self._h, ctypes.byref(thr), ms.ctypes.data))
+        return thr.value, ms
+
+
+def batch_create(models, flags: int = 0) -> Batch:
+    descs = (L.ModelDesc * len(models))()
+    keep = []
+    for i, m in enumerate(models):
+        d, k = model_desc(m)
+        descs[i] = d
+        keep.append(k)
+    h = ctypes.c_void_p()
+    L.check(L.load().ed_batch_create(descs, len(models), int(flags), ctypes.byref(h)))
+    return Batch(h.value, models)
+
+
+def batch_apply(b: Batch, x, y, stream=None):
+    import torch
+
+    for t, nm in ((x, "x"), (y, "y")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or t.numel() != b.dim:
+            raise ValueError(f"{nm} must be a float32 CUDA tensor with {b.dim} elements")
+    L.check(L.load().ed_batch_apply(b.handle, _ptr(x), _ptr(y), L.ED_F32, _stream_handle(stream)))
+    return y
+
+
+def batch_lanczos(b: Batch, max_iter: int = 400, tol: float = 1e-7, check_every: int = 5, seed: int = 20260507):
+    o = L.LanczosOpts()
+    L.load().ed_lanczos_default_opts(ctypes.byref(o))
+    o.mode = L.ED_LZ_F32
+    o.max_iter = int(max_iter)
+    o.tol = float(tol)
+    o.check_every = int(check_every)
+    o.seed = int(seed)
+    n = len(b.models)
+    e0 = np.zeros(n)
+    it = np.zeros(n, np.int32)
+    r = L.Report()
+    st = L.load().ed_batch_lanczos(b.handle, ctypes.byref(o), e0.ctypes.data, it.ctypes.data, ctypes.byref(r))
+    if st not in (L.ED_OK, L.ED_ENOCONV):
+        L.check(st)
+    return e0, it, {"steps": r.iterations, "seconds": r.seconds, "all_converged": bool(r.converged), "status": st}
+
+
+class Server:
+    """Continuous-batching request loop (``ed_server*``)."""
+
+    def __init__(self, device_bytes: int = 1 << 30, max_slots: int = 256, max_iter: int = 400, check_every: int = 5,
+                 tol: float = 1e-7, seed: int = 20260507, inject_alloc_failures: int = 0):
+        o = L.ServerOpts()
+        L.load().ed_server_default_opts(ctypes.byref(o))
+        o.device_bytes = int(device_bytes)
+        o.max_slots = int(max_slots)
+        o.max_iter = int(max_iter)
+        o.check_every = int(check_every)
+        o.tol = float(tol)
+        o.seed = int(seed)
+        o.inject_alloc_failures = int(inject_alloc_failures)
+        h = ctypes.c_void_p()
+        L.check(L.load().ed_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, model) -> int:
+        d, keep = model_desc(model)
+        t = ctypes.c_uint64()
+        L.check(L.load().ed_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        r = L.Result()
+        st = L.load().ed_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r))
+        if st != L.ED_OK:
+            L.check(st)
+        return {"e0": r.e0, "iterations": r.iterations, "converged": bool(r.converged), "status": r.status,
+                "latency_s": r.latency_s, "queue_s": r.queue_s, "run_s": r.run_s}
+
+    def cancel(self, ticket: int):
+        L.check(L.load().ed_server_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def stats(self) -> dict:
+        s = L.ServerStats()
+        L.check(L.load().ed_server_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in L.ServerStats._fields_}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            L.load().ed_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

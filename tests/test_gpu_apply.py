@@ -42,6 +42,9 @@ def _models():
         "hub_2x3_torus": W.hubbard_torus(2, 3, 1.0, 5.0, 2, 3),
         "hub_open_3x4": W.hubbard_open_cluster(3, 4, 1.0, 6.0, tp=-0.2, eps=rng.uniform(-1, 1, 12), n_up=5, n_dw=7),
         "hub_empty_dw": W.hubbard_chain(7, 1.0, 2.0, 3, 0),
+        "hub12_particle": W.hubbard_chain(12, 1.0, 4.0, 7, 6),
+        "hub12_hole": W.hubbard_chain(12, 1.0, 4.0, 5, 6),
+        "hub_rect_dyadic": W.hubbard_torus(2, 4, 1.0, 2.0, 3, 5),
         "hub_site_U": W.Model("hubbard", 5, W.chain_bonds(5, True), t=1.0, U=[1.0, 2.0, 3.0, 1.0, 0.0],
                               eps=[0.1, -0.2, 0.3, 0.0, 0.5], n_up=2, n_dw=3, spin_cut=True),
     }

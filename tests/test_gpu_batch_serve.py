@@ -1,0 +1,160 @@
+"""Batched and served Lanczos (FP32 storage, FP64 reductions) through the C ABI.
+
+Tolerances: FP32-storage H|psi> relative L2 <= 1e-6 (as for the single
+apply); FP32-storage ground-state energies within 2e-6 relative of the
+oracle (FP32 vectors limit the Ritz value to a few FP32 ulps).  Results of a
+request alone and in a mix must agree exactly: every instance's recurrence
+uses only its own data, with fixed reduction order and convergence checks at
+fixed iteration counts.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ed():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_07621_gb300 as ed
+
+    return ed
+
+
+def _instances(n=24, max_dim=60000, seed=20260507):
+    out = []
+    for m in W.batched_hubbard_instances(512, seed):
+        from math import comb
+
+        if comb(m.n_sites, m.n_up) * comb(m.n_sites, m.n_dw) <= max_dim:
+            out.append(m)
+        if len(out) == n:
+            break
+    return out
+
+
+def test_batch_apply_parity(ed, oracle_mod):
+    import torch
+
+    ms = _instances(24)
+    b = ed.batch_create(ms)
+    off = b.offsets()
+    x = np.zeros(b.dim)
+    refs = []
+    for i, m in enumerate(ms):
+        keys = ed.build_sectors(m).state_keys()
+        x[off[i]:off[i + 1]] = W.start_values(keys)
+        ok = oracle_mod.sector_keys(m)
+        pos = oracle_mod.find_keys(m, ok, keys)
+        refs.append(oracle_mod.apply_H(m, ok, W.start_values(ok))[pos])
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.zeros_like(xt)
+    ed.batch_apply(b, xt, yt)
+    torch.cuda.synchronize()
+    y = yt.double().cpu().numpy()
+    for i in range(len(ms)):
+        r = refs[i]
+        err = np.linalg.norm(y[off[i]:off[i + 1]] - r) / np.linalg.norm(r)
+        assert err <= 1e-6, (i, ms[i].name, err)
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_batch_lanczos_vs_oracle(ed, oracle_mod, flags):
+    ms = _instances(16, max_dim=8000)
+    b = ed.batch_create(ms, flags=flags)
+    thr, tune = b.info()
+    assert thr in (0, 8, 16, 32, 64)
+    if flags == 0:
+        assert (tune > 0).all()
+    e, it, info = ed.batch_lanczos(b, tol=1e-7)
+    assert info["all_converged"]
+    for i, m in enumerate(ms):
+        keys = oracle_mod.sector_keys(m)
+        if len(keys) <= 2500:
+            ref = np.linalg.eigvalsh(oracle_mod.dense_H(m, keys))[0]
+        else:
+            ref, _, _ = oracle_mod.ground_state(m, keys, n_iter=300)
+        assert abs(e[i] - ref) <= 2e-6 * max(1.0, abs(ref)), (i, m.name, e[i], ref)
+
+
+def test_batch_matches_single_instance_runs(ed):
+    """The same instance gives the same energy in a batch of 1 and in a batch of many."""
+    ms = _instances(12, max_dim=20000)
+    b = ed.batch_create(ms, flags=1)
+    e_all, _, _ = ed.batch_lanczos(b, tol=1e-7)
+    for i in (0, 5, 11):
+        b1 = ed.batch_create([ms[i]], flags=1)
+        e1, _, _ = ed.batch_lanczos(b1, tol=1e-7)
+        assert e1[0] == e_all[i]
+
+
+def test_serving_mix_equals_alone(ed):
+    ms = _instances(20, max_dim=20000)
+    # alone: one request at a time
+    alone = []
+    with_srv = ed.Server(device_bytes=256 << 20, max_slots=1, check_every=5, tol=1e-7)
+    for m in ms[:6]:
+        t = with_srv.submit(m)
+        alone.append(with_srv.wait(t, 60000)["e0"])
+    with_srv.close()
+    # mixed: staggered arrivals into few slots, so requests queue and overlap
+    srv = ed.Server(device_bytes=256 << 20, max_slots=4, check_every=5, tol=1e-7)
+    tickets = []
+    for m in ms:
+        tickets.append(srv.submit(m))
+        time.sleep(0.002)
+    res = [srv.wait(t, 120000) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    for i in range(6):
+        assert res[i]["e0"] == alone[i], (i, res[i]["e0"], alone[i])
+    assert all(r["converged"] for r in res)
+    assert st["completed"] == len(ms) and st["failed"] == 0
+    assert st["p99_s"] >= st["p50_s"] > 0
+    # with 4 slots and 20 requests some had to wait for a free slot
+    assert max(r["queue_s"] for r in res) > 0
+
+
+def test_serving_faults_on_host(ed):
+    from paper_2605_07621_gb300 import EDError
+
+    ms = _instances(6, max_dim=5000)
+    srv = ed.Server(device_bytes=8 << 20, max_slots=2, inject_alloc_failures=2)
+    t = [srv.submit(m) for m in ms]
+    with pytest.raises(EDError, match="ED_ENOMEM"):
+        srv.wait(t[0], 60000)
+    with pytest.raises(EDError, match="ED_ENOMEM"):
+        srv.wait(t[1], 60000)
+    for k in t[2:]:
+        assert srv.wait(k, 60000)["converged"]
+    # a request larger than the whole budget is refused at submission
+    big = W.config_hub12()
+    with pytest.raises(EDError, match="ED_ENOMEM"):
+        srv.submit(big)
+    # spin models are not served (single-block Hubbard requests only)
+    with pytest.raises(EDError, match="ED_EUNSUPPORTED"):
+        srv.submit(W.heisenberg_chain(8))
+    srv.close()
+
+
+def test_serving_timeout_and_cancel(ed):
+    from paper_2605_07621_gb300 import EDError
+
+    ms = _instances(8, max_dim=20000)
+    srv = ed.Server(device_bytes=256 << 20, max_slots=1)
+    t = [srv.submit(m) for m in ms]
+    with pytest.raises(EDError, match="ED_ETIMEOUT"):
+        srv.wait(t[-1], 0)
+    srv.cancel(t[-1])
+    with pytest.raises(EDError, match="ED_ECANCELLED"):
+        srv.wait(t[-1], 60000)
+    for k in t[:-1]:
+        assert srv.wait(k, 60000)["converged"]
+    srv.close()
