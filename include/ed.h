@@ -226,6 +226,18 @@ ed_status ed_server_get_stats(ed_server* s, ed_server_stats* out);
 /* stops the worker after its current step and frees the device arena */
 void ed_server_destroy(ed_server* s);
 
+/* ---- tracing ------------------------------------------------------------
+ * Per-stage CUDA-event timing of ed_apply_H.  While enabled, every apply
+ * records events on the caller's stream around its stages: 0 = exponent of
+ * max|x|, 1 = fixed-point copy (both only on the exact FP64 path), 2 = row
+ * pass (diagonal, H_B, cross terms), 3 = H_A panel pass.  ed_profile_read
+ * waits for the recorded applies and returns the accumulated milliseconds
+ * per stage (ms: host array of 4) and the number of applies; reset != 0
+ * clears the totals.  Applies that do not use the class-sorted kernels
+ * record nothing. */
+ed_status ed_profile_enable(ed_ctx* ctx, int enable);
+ed_status ed_profile_read(ed_ctx* ctx, double* ms, int64_t* count, int reset);
+
 /* ---- queries ---------------------------------------------------------- */
 int64_t ed_dim(const ed_ctx* ctx);
 int ed_num_blocks(const ed_ctx* ctx);

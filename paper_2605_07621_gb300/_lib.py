@@ -82,6 +82,8 @@ SIGNATURES = [
     ("ed_server_cancel", c_int, [c_void_p, c_uint64]),
     ("ed_server_get_stats", c_int, [c_void_p, P(ServerStats)]),
     ("ed_server_destroy", None, [c_void_p]),
+    ("ed_profile_enable", c_int, [c_void_p, c_int]),
+    ("ed_profile_read", c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     ("ed_dim", c_int64, [c_void_p]),
     ("ed_num_blocks", c_int, [c_void_p]),
     ("ed_blocks", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -32,6 +32,14 @@ struct P3 {
 struct PF32 {
   using S = float;
   __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
+  __device__ static float bw(const Dev3& t, int k) { return t.bond_w32[k]; }
+  __device__ static float diagA(const Dev3& t, long long gA) { return t.A_d32[gA] + t.dc0_32; }
+  __device__ static float diagB(const Dev3& t, long long gB) { return t.B_d32[gB]; }
+  __device__ static float vab(const Dev3& t, unsigned z) {
+    float v = 0.f;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
+    return v;
+  }
   __device__ static float diag(const Dev3& t, long long gA, long long gB, unsigned z) {
     float v = t.A_d32[gA] + t.B_d32[gB] + t.dc0_32;
     for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
@@ -41,6 +49,14 @@ struct PF32 {
 struct PF64 {
   using S = double;
   __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
+  __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
+  __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
+  __device__ static double diagB(const Dev3& t, long long gB) { return t.B_d64[gB]; }
+  __device__ static double vab(const Dev3& t, unsigned z) {
+    double v = 0.0;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
+    return v;
+  }
   __device__ static double diag(const Dev3& t, long long gA, long long gB, unsigned z) {
     double v = t.A_d64[gA] + t.B_d64[gB] + t.dc0_64;
     for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
@@ -50,6 +66,14 @@ struct PF64 {
 struct PI64 {
   using S = long long;
   __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
+  __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
+  __device__ static long long diagA(const Dev3& t, long long gA) { return (long long)t.A_dI[gA] + t.dc0_I; }
+  __device__ static long long diagB(const Dev3& t, long long gB) { return (long long)t.B_dI[gB]; }
+  __device__ static long long vab(const Dev3& t, unsigned z) {
+    long long v = 0;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
+    return v;
+  }
   __device__ static long long diag(const Dev3& t, long long gA, long long gB, unsigned z) {
     long long v = (long long)t.A_dI[gA] + (long long)t.B_dI[gB] + t.dc0_I;
     for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
@@ -212,20 +236,23 @@ __device__ __forceinline__ int find_blk(const long long* row_start, int nblk, lo
 constexpr int kRowThreads = 512;
 
 // Row pass: work unit = R consecutive rows of one block ("row group").  The
-// rows are brought into shared memory by bulk TMA copies; two CTAs share an
-// SM so that one CTA's copy overlaps the other's compute.  Per column b the
-// class-sorted CSR indices of H_B are read once and gathered from all R
-// rows; index loads are issued four at a time.
+// rows are brought into shared memory by bulk TMA copies (two CTAs per SM,
+// so one CTA's copy overlaps the other's compute).  Per column b:
+//  * H_B: the class segments of the column's index list are padded to
+//    groups of four 16-bit indices, read with one 8-byte load per group and
+//    gathered from all R staged rows (padding points at a zero slot);
+//  * cross terms: one B-side map load per B cross site, shared by the R
+//    rows, then one gather per valid bond from the neighbouring block;
+//  * the diagonal from per-row constants and popcounts of packed words.
 template <class Pol, int R>
 __global__ void __launch_bounds__(kRowThreads, 2)
-    k_row4(P3 p, const long long* __restrict__ grp_start, long long n_groups, const typename Pol::S* __restrict__ x,
+    k_row5(P3 p, const long long* __restrict__ grp_start, long long n_groups, const typename Pol::S* __restrict__ x,
            typename Pol::S* __restrict__ y, const int* __restrict__ emax, long long stage_elems, int* err) {
   using S = typename Pol::S;
-  extern __shared__ __align__(16) unsigned char smem4[];
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem4);
-  S* bufs = reinterpret_cast<S*>(smem4 + 128);
-  __shared__ const S* src_row[R][32];
-  __shared__ int src_ib[32];
+  extern __shared__ __align__(16) unsigned char smem5[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem5);
+  S* bufs = reinterpret_cast<S*>(smem5 + 128);
+  __shared__ const S* src_row[R][32];  // per row, per A cross site
   __shared__ int s_pad[R];
   constexpr int V = 16 / (int)sizeof(S);
   const Dev3& t = p.t;
@@ -241,8 +268,7 @@ __global__ void __launch_bounds__(kRowThreads, 2)
     const DevBlock bl = p.blocks[bi];
     const long long a0 = (g - grp_start[bi]) * R;
     const int nr = (int)min((long long)R, bl.dA - a0);
-    const long long dB = bl.dB;
-    // start the bulk copies of the group's rows
+    const int dB = (int)bl.dB;
     if (threadIdx.x == 0) {
       proxy_fence();
       unsigned bytes = 0;
@@ -264,14 +290,16 @@ __global__ void __launch_bounds__(kRowThreads, 2)
         bar_arrive(&bar[0]);
       }
     }
-    // ragged ends of each row, plain loads
     for (int r = 0; r < nr; ++r) {
       const long long g0 = bl.off + (a0 + r) * dB;
       const long long gend = g0 + dB;
       const long long gal = (g0 + V - 1) / V * V, galend = gend / V * V;
       const int pad = (int)(g0 % V);
       S* buf = bufs + r * stage_elems;
-      if (threadIdx.x == 0) s_pad[r] = pad;
+      if (threadIdx.x == 0) {
+        s_pad[r] = pad;
+        buf[pad + dB] = (S)0;  // zero slot addressed by the padding indices
+      }
       if (galend > gal) {
         for (long long q = g0 + threadIdx.x; q < gal; q += blockDim.x) buf[pad + (q - g0)] = x[q];
         for (long long q = galend + threadIdx.x; q < gend; q += blockDim.x) buf[pad + (q - g0)] = x[q];
@@ -279,23 +307,27 @@ __global__ void __launch_bounds__(kRowThreads, 2)
         for (long long q = g0 + threadIdx.x; q < gend; q += blockDim.x) buf[pad + (q - g0)] = x[q];
       }
     }
-    // cross-cut source rows, one per (row, cross bond)
+    // neighbouring-block source row of each (row, A cross site)
     if (threadIdx.x < 32 * R) {
-      const int r = threadIdx.x >> 5, k = threadIdx.x & 31;
+      const int r = threadIdx.x >> 5, ia = threadIdx.x & 31;
       const S* sp = nullptr;
-      if (r < nr && k < p.ncross) {
+      if (r < nr && ia < 32 && p.ncross) {
         const long long gA = bl.gA0 + a0 + r;
-        const unsigned pa = t.A_pack[gA];
-        const DevCross cr = p.cross[k];
-        const int sb = ((pa >> k) & 1u) ? bl.nbr_lo : bl.nbr_hi;
-        if (sb >= 0) {
-          const DevBlock so = p.blocks[sb];
-          const unsigned rr = t.mapA[(long long)cr.ia * t.A_total + gA];
-          if (rr != 0xFFFFu) sp = x + so.off + (long long)rr * so.dB;
+        // which bond touches site ia: any bond k with bond_ia[k] == ia gives its A bit
+        int k = -1;
+        for (int q = 0; q < p.ncross; ++q)
+          if (t.bond_ia[q] == ia) { k = q; break; }
+        if (k >= 0) {
+          const unsigned pa = t.A_pack[gA];
+          const int sb = ((pa >> k) & 1u) ? bl.nbr_lo : bl.nbr_hi;
+          if (sb >= 0) {
+            const DevBlock so = p.blocks[sb];
+            const unsigned rr = t.mapA[(long long)ia * t.A_total + gA];
+            if (rr != 0xFFFFu) sp = x + so.off + (long long)rr * so.dB;
+          }
         }
-        if (r == 0) src_ib[k] = cr.ib;
       }
-      src_row[r][k] = sp;
+      src_row[r][ia] = sp;
     }
     const bool ok = bar_wait(&bar[0], phase);
     if (__syncthreads_or(!ok)) {
@@ -306,64 +338,67 @@ __global__ void __launch_bounds__(kRowThreads, 2)
     phase ^= 1;
     unsigned pa[R];
     const S* xs[R];
+    S da[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int rr = r < nr ? r : 0;
-      pa[r] = t.A_pack[bl.gA0 + a0 + rr];
+      const long long gA = bl.gA0 + a0 + rr;
+      pa[r] = t.A_pack[gA];
       xs[r] = bufs + rr * stage_elems + s_pad[rr];
+      da[r] = Pol::diagA(t, gA);
     }
     const bool final_ = !bl.has_hA;
-    for (long long b = threadIdx.x; b < dB; b += blockDim.x) {
-      const long long gB = bl.gB0 + b;
-      const uint2 m = t.B_meta[gB];
+    const long long gB0 = bl.gB0;
+    for (int b = threadIdx.x; b < dB; b += blockDim.x) {
+      const long long gB = gB0 + b;
+      const uint2 m = t.B_meta4[gB];
       const unsigned pb = t.B_pack[gB];
+      const S dbv = Pol::diagB(t, gB);
       S acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const unsigned z = t.vab_and ? (pa[r] & pb) : (pa[r] ^ pb);
-        acc[r] = Pol::diag(t, bl.gA0 + a0 + (r < nr ? r : 0), gB, z) * xs[r][b];
+        acc[r] = (da[r] + dbv + Pol::vab(t, z)) * xs[r][b];
       }
-      unsigned e = m.x;
+      const uint2* cp = t.B_col4 + m.x;
 #pragma unroll
       for (int c = 0; c < kMaxCls; ++c) {
-        const unsigned n = (m.y >> (8 * c)) & 255u;
-        if (!n) continue;
+        const unsigned n4 = (m.y >> (8 * c)) & 255u;
+        if (!n4) continue;
         S sum[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) sum[r] = 0;
-        unsigned i = 0;
-        for (; i + 4 <= n; i += 4) {
-          const unsigned c0 = t.B_col[e + i], c1 = t.B_col[e + i + 1], c2 = t.B_col[e + i + 2], c3 = t.B_col[e + i + 3];
+        for (unsigned i = 0; i < n4; ++i) {
+          const uint2 q = __ldg(cp + i);
+          const unsigned i0 = q.x & 0xFFFFu, i1 = q.x >> 16, i2 = q.y & 0xFFFFu, i3 = q.y >> 16;
 #pragma unroll
-          for (int r = 0; r < R; ++r) sum[r] += (xs[r][c0] + xs[r][c1]) + (xs[r][c2] + xs[r][c3]);
+          for (int r = 0; r < R; ++r) sum[r] += (xs[r][i0] + xs[r][i1]) + (xs[r][i2] + xs[r][i3]);
         }
-        for (; i < n; ++i) {
-          const unsigned c0 = t.B_col[e + i];
-#pragma unroll
-          for (int r = 0; r < R; ++r) sum[r] += xs[r][c0];
-        }
-        e += n;
+        cp += n4;
         const S wc = Pol::w(t, c);
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] += wc * sum[r];
       }
       if (p.ncross) {
+        unsigned dr[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (r >= nr) break;
-          const unsigned diff = pa[r] ^ pb;
+        for (int r = 0; r < R; ++r) dr[r] = r < nr ? (pa[r] ^ pb) : 0u;
+        for (int ib = 0; ib < t.n_ib; ++ib) {
+          const unsigned rm = t.ib_mask[ib];
+          unsigned any = 0;
 #pragma unroll
-          for (int c = 0; c < kMaxCls; ++c) {
-            unsigned dd = diff & t.cross_cls_mask[c];
-            if (!dd) continue;
-            S sum = 0;
+          for (int r = 0; r < R; ++r) any |= dr[r] & rm;
+          if (!any) continue;
+          const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            unsigned dd = dr[r] & rm;
             while (dd) {
               const int k = __ffs(dd) - 1;
               dd &= dd - 1;
-              const S* sp = src_row[r][k];
-              if (sp) sum += __ldg(sp + t.mapB[(long long)src_ib[k] * t.B_total + gB]);
+              const S* sp = src_row[r][t.bond_ia[k]];
+              if (sp) acc[r] += Pol::bw(t, k) * __ldg(sp + mq);
             }
-            acc[r] += Pol::w(t, c) * sum;
           }
         }
       }
@@ -456,7 +491,7 @@ static int rows_per_pass(size_t es) { return es == 4 ? 2 : 1; }
 static size_t v3_smem(const ed_ctx* c, size_t es, long long* stage_elems) {
   long long mdb = 1;
   for (const auto& b : c->blocks) mdb = std::max<long long>(mdb, b.dB);
-  *stage_elems = ((mdb + 16 / (long long)es + 15) / 16) * 16;
+  *stage_elems = ((mdb + 1 + 16 / (long long)es + 15) / 16) * 16;  // row, zero slot, alignment pad
   return 128 + (size_t)rows_per_pass(es) * (size_t)(*stage_elems) * es;
 }
 
@@ -466,21 +501,42 @@ bool v3_usable(const ed_ctx* c, ed_dtype dt, const void* x) {
   return v3_smem(c, dt == ED_F64 ? 8 : 4, &se) <= 110 * 1024;
 }
 
+// events bracketing the stages of one apply when profiling is on
+struct ProfMarks {
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool on = false;
+  void begin(ed_ctx* c) {
+    on = c->prof;
+    if (!on) return;
+    for (auto& e : ev) cudaEventCreate(&e);
+  }
+  void mark(int i, cudaStream_t st) {
+    if (on) cudaEventRecord(ev[i], st);
+  }
+  void end(ed_ctx* c) {
+    if (!on) return;
+    for (auto& e : ev) c->prof_ev.push_back(e);
+  }
+};
+
 template <class Pol>
-static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y, const int* emax, cudaStream_t st) {
+static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y, const int* emax, cudaStream_t st,
+                        ProfMarks& pm) {
   P3 p = make_p3(c);
   if (p.n_rows == 0) return ED_OK;
   long long se;
   constexpr int R = sizeof(typename Pol::S) == 4 ? 2 : 1;
   const size_t smem = v3_smem(c, sizeof(typename Pol::S), &se);
-  auto kern = k_row4<Pol, R>;
+  auto kern = k_row5<Pol, R>;
   ED_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int sms = n_sms(c->device);
   const long long* gs = R == 2 ? c->d_grp2_start : c->d_row_start;
   const long long ng = R == 2 ? c->n_grp2 : c->n_rows;
   const long long grid = std::min<long long>(ng, (long long)sms * 2);
+  pm.mark(2, st);
   kern<<<(unsigned)grid, kRowThreads, smem, st>>>(p, gs, ng, x, y, emax, se, c->d_err);
   ED_CUDA_TRY(cudaGetLastError());
+  pm.mark(3, st);
   if (c->n_panel_items > 0) {
     const long long g2 = std::min<long long>(c->n_panel_items, (long long)sms * 8);
     k_panel3<Pol><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
@@ -489,19 +545,71 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
   return ED_OK;
 }
 
-ed_status apply_v3(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t st) {
-  if (dt == ED_F32) return run_v3<PF32>(c, (const float*)x, (float*)y, nullptr, st);
-  if (!c->dyadic) return run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st);
-  // exact fixed point: exponent of max|x|, scaled copy, integer passes
-  if (!c->d_fixed) ED_TRY(dev_alloc(c, (void**)&c->d_fixed, (size_t)std::max<long long>(c->D, 2) * 8));
+// exact fixed-point FP64 apply with explicit scratch: `fixed` holds D
+// 64-bit integers, `emax` one int (cleared here before use)
+static ed_status apply_fixed(ed_ctx* c, const double* x, double* y, long long* fixed, int* emax, cudaStream_t st,
+                             ProfMarks& pm) {
   const long long n = c->D;
-  ED_CUDA_TRY(cudaMemsetAsync(c->d_exp, 0, sizeof(int), st));
+  ED_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int), st));
   const int sms = n_sms(c->device);
   const long long g = std::min<long long>((n + 255) / 256, (long long)sms * 8);
-  k_exp_max<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>((const double*)x, n, c->d_exp);
-  k_to_fixed<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>((const double*)x, c->d_fixed, n, c->d_exp, c->t3.P);
+  pm.mark(0, st);
+  k_exp_max<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>(x, n, emax);
+  pm.mark(1, st);
+  k_to_fixed<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>(x, fixed, n, emax, c->t3.P);
   ED_CUDA_TRY(cudaGetLastError());
-  return run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st);
+  return run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm);
+}
+
+ed_status apply_v3(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t st) {
+  ProfMarks pm;
+  pm.begin(c);
+  ed_status r;
+  if (dt == ED_F32 || !c->dyadic) {
+    pm.mark(0, st);
+    pm.mark(1, st);
+    r = dt == ED_F32 ? run_v3<PF32>(c, (const float*)x, (float*)y, nullptr, st, pm)
+                     : run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st, pm);
+  } else {
+    // exact fixed point: exponent of max|x|, scaled copy, integer passes
+    if (!c->d_fixed) ED_TRY(dev_alloc(c, (void**)&c->d_fixed, (size_t)std::max<long long>(c->D, 2) * 8));
+    r = apply_fixed(c, (const double*)x, (double*)y, c->d_fixed, c->d_exp, st, pm);
+  }
+  pm.mark(4, st);
+  pm.end(c);
+  return r;
 }
 
 }  // namespace edk
+
+using namespace edk;
+
+extern "C" ed_status ed_profile_enable(ed_ctx* c, int enable) {
+  if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }
+  c->prof = enable != 0;
+  return ED_OK;
+}
+
+extern "C" ed_status ed_profile_read(ed_ctx* c, double* ms, int64_t* count, int reset) {
+  if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }
+  for (size_t i = 0; i + 5 <= c->prof_ev.size(); i += 5) {
+    cudaEvent_t* e = &c->prof_ev[i];
+    ED_CUDA_TRY(cudaEventSynchronize(e[4]));
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.f;
+      ED_CUDA_TRY(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+      c->prof_ms[k] += t;
+    }
+    ++c->prof_count;
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(e[k]);
+  }
+  c->prof_ev.clear();
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = c->prof_ms[k];
+  if (count) *count = c->prof_count;
+  if (reset) {
+    for (double& v : c->prof_ms) v = 0.0;
+    c->prof_count = 0;
+  }
+  return ED_OK;
+}

@@ -147,6 +147,17 @@ struct Dev3 {
   unsigned cross_cls_mask[kMaxCls];  // cross bonds (bit k) with off-diagonal class c
   int q_shift;              // values * 2^q_shift are integers (fixed-point path)
   int P;                    // fraction bits of the fixed-point vector
+  // padded side-B lists of the row pass: every class segment starts at a
+  // multiple of 4 entries and is padded to one with the zero-slot index d_B
+  const uint2* B_meta4;     // x: first entry / 4, y: per-class group-of-4 counts
+  const uint2* B_col4;      // 4 x uint16 per element
+  // cross bonds grouped by B site: bonds with B site ib are bits ib_mask[ib]
+  int n_ib;
+  unsigned ib_mask[32];
+  unsigned char bond_ia[32];
+  float bond_w32[32];
+  double bond_w64[32];
+  long long bond_wI[32];
 };
 
 struct DevDiagParams {
@@ -206,6 +217,11 @@ struct ed_ctx {
   long long* d_fixed = nullptr;      // fixed-point copy of x (lazily allocated, D entries)
   int* d_exp = nullptr;              // exponent scratch of the fixed-point path
   std::vector<int> cross_cls;        // class of each cross bond
+  // per-stage CUDA-event timing of apply_H (ed_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // 5 events per recorded apply
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_count = 0;
   // per-side CSR stats
   int64_t nnzA = 0, nnzB = 0;
   // Lanczos / GF work buffers (lazily allocated)

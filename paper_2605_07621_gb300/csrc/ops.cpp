@@ -110,7 +110,36 @@ struct Side3 {
   std::vector<uint16_t> col;
   std::vector<uint32_t> pack;
   std::vector<int> dI;
+  std::vector<uint2> meta4;
+  std::vector<uint16_t> col4;
 };
+
+// padded copy: class segments start at multiples of 4 entries and are filled
+// up with `zero_idx` (an always-zero slot after the row in shared memory)
+bool build_padded(const Side& sd, Side3& o) {
+  const int64_t tot = (int64_t)o.meta.size();
+  o.meta4.resize(tot);
+  o.col4.clear();
+  for (int k = 0; k <= sd.n; ++k) {
+    if (!sd.used[k]) continue;
+    const uint16_t zero_idx = (uint16_t)sd.dim(k);
+    for (int64_t g = sd.start[k]; g < sd.start[k + 1]; ++g) {
+      const uint2 m = o.meta[g];
+      if (o.col4.size() / 4 > 0xFFFFFFFFull) return false;
+      const uint32_t start4 = (uint32_t)(o.col4.size() / 4);
+      uint32_t e = m.x, packed = 0;
+      for (int c = 0; c < kMaxCls; ++c) {
+        const uint32_t n = (m.y >> (8 * c)) & 255u;
+        const uint32_t n4 = (n + 3) / 4;
+        for (uint32_t i = 0; i < 4 * n4; ++i) o.col4.push_back(i < n ? o.col[e + i] : zero_idx);
+        e += n;
+        packed |= n4 << (8 * c);
+      }
+      o.meta4[g] = make_uint2(start4, packed);
+    }
+  }
+  return true;
+}
 
 // class-sorted copy of one side's CSR
 bool build_side3(const HostSideOps& h, const std::vector<double>& cls_val, Side3& o) {
@@ -159,6 +188,9 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   if (cls.size() > (size_t)kMaxCls) return ED_OK;
   Side3 a3, b3;
   if (!build_side3(ha, cls, a3) || !build_side3(hb, cls, b3)) return ED_OK;
+  for (const Block& b : c->blocks)
+    if (b.dB >= 65535) return ED_OK;  // the zero slot index d_B must fit 16 bits
+  if (!build_padded(c->B, b3)) return ED_OK;
   Dev3& t = c->t3;
   t = Dev3{};
   for (size_t i = 0; i < cls.size(); ++i) {
@@ -170,7 +202,12 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
     int ci = (int)(std::find(cls.begin(), cls.end(), c->cross[k].coef) - cls.begin());
     c->cross_cls[k] = ci;
     t.cross_cls_mask[ci] |= 1u << k;
+    t.ib_mask[c->cross[k].ib] |= 1u << k;
+    t.bond_ia[k] = (unsigned char)c->cross[k].ia;
+    t.bond_w64[k] = c->cross[k].coef;
+    t.bond_w32[k] = (float)c->cross[k].coef;
   }
+  t.n_ib = (int)c->crossB_bits.size();
   const DevDiagParams& dp = c->diag;
   t.vab_and = dp.vab_and;
   t.ncls_d = dp.ncls;
@@ -197,6 +234,7 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   if (qs >= 0) {
     t.q_shift = qs;
     for (size_t i = 0; i < cls.size(); ++i) t.wI[i] = (long long)std::ldexp(cls[i], qs);
+    for (size_t k = 0; k < c->cross.size(); ++k) t.bond_wI[k] = (long long)std::ldexp(c->cross[k].coef, qs);
     for (int q = 0; q < dp.ncls; ++q) t.dwI[q] = (long long)std::ldexp(dp.w[q], qs);
     t.dc0_I = (long long)std::ldexp(dp.c0, qs);
     a3.dI.resize(ha.diag.size());
@@ -240,6 +278,15 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   for (size_t i = 0; i < mb.size(); ++i) mb[i] = hb.maps[i] < 0 ? 0xFFFF : (uint16_t)hb.maps[i];
   ED_TRY(upload(c, &mA, ma));
   ED_TRY(upload(c, &mB, mb));
+  uint2 *Bm4, *Bc4;
+  {
+    std::vector<uint2> c4(b3.col4.size() / 4);
+    std::memcpy(c4.data(), b3.col4.data(), b3.col4.size() * sizeof(uint16_t));
+    ED_TRY(upload(c, &Bm4, b3.meta4));
+    ED_TRY(upload(c, &Bc4, c4));
+  }
+  t.B_meta4 = Bm4;
+  t.B_col4 = Bc4;
   t.A_meta = Am; t.B_meta = Bm; t.A_col = Ac; t.B_col = Bc; t.A_pack = Ap; t.B_pack = Bp;
   t.A_dI = AdI; t.B_dI = BdI; t.mapA = mA; t.mapB = mB;
   t.A_d32 = c->tab.A_diag32; t.B_d32 = c->tab.B_diag32; t.A_d64 = c->tab.A_diag; t.B_d64 = c->tab.B_diag;

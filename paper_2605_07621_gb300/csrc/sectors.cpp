@@ -248,6 +248,12 @@ extern "C" ed_status ed_build_sectors(const ed_model_desc* m, ed_ctx** out) {
     if (fb == c->crossB_bits.end()) { cb.ib = (int)c->crossB_bits.size(); c->crossB_bits.push_back(cb.q); }
     else cb.ib = (int)(fb - c->crossB_bits.begin());
   }
+  // bond k is bit k of the packed cross words; order the bonds by their B
+  // site (then A site) so that the bonds of one B site are a contiguous bit
+  // range and a kernel loads each B-side map entry once per column
+  std::stable_sort(c->cross.begin(), c->cross.end(), [](const CrossBond& x, const CrossBond& y) {
+    return x.ib != y.ib ? x.ib < y.ib : x.ia < y.ia;
+  });
   // diagonal cross term V_AB(a,b) as weighted popcounts of packed bit words
   DevDiagParams dp{};
   if (c->kind == ED_SPIN) {

@@ -86,6 +86,17 @@ class Context:
     def device_bytes(self) -> int:
         return int(L.load().ed_device_bytes(self._h))
 
+    def profile(self, enable: bool = True):
+        """Per-stage CUDA-event timing of apply_H (see ed_profile_enable)."""
+        L.check(L.load().ed_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self, reset: bool = True):
+        """(ms per stage [exp_max, to_fixed, row pass, panel pass], number of applies)."""
+        ms = np.zeros(4)
+        n = ctypes.c_int64()
+        L.check(L.load().ed_profile_read(self._h, ms.ctypes.data, ctypes.byref(n), 1 if reset else 0))
+        return ms, n.value
+
 
 def model_desc(model):
     """ed_model_desc from any object with the fields of ``workloads.Model``;

@@ -24,6 +24,7 @@ from .lattices import (  # noqa: F401
     config_hub12,
     config_j1j2_4x8,
     config_hub4x4,
+    config_j1j2_4x7,
     CONFIG_NAMES,
     config_by_name,
 )

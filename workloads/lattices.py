@@ -314,9 +314,17 @@ def config_hub4x4() -> Model:
     return m
 
 
-CONFIG_NAMES = ("heis16", "hub12", "j1j2_4x8", "hub4x4")
+def config_j1j2_4x7() -> Model:
+    """Smaller J1-J2 torus (Lx=7, Ly=4, 40,116,600 states, cut 14|14) used
+    for detailed kernel profiles: same kernels, vectors still larger than L2."""
+    m = j1j2_torus(7, 4, 1.0, 0.5, 14, (1 << 14) - 1)
+    m.name = "j1j2_4x7"
+    return m
+
+
+CONFIG_NAMES = ("heis16", "hub12", "j1j2_4x8", "hub4x4", "j1j2_4x7")
 
 
 def config_by_name(name: str) -> Model:
     return {"heis16": config_heis16, "hub12": config_hub12, "j1j2_4x8": config_j1j2_4x8,
-            "hub4x4": config_hub4x4}[name]()
+            "hub4x4": config_hub4x4, "j1j2_4x7": config_j1j2_4x7}[name]()
