@@ -98,6 +98,24 @@ ed_status ed_build_local_ops(ed_ctx* ctx, int flags);
  * `stream` (cudaStream_t, NULL = legacy default stream); no sync. */
 ed_status ed_apply_H(ed_ctx* ctx, const void* x, void* y, ed_dtype dtype, void* stream);
 
+/* y = H x like ed_apply_H with ED_F64, for callers that cannot allocate
+ * device memory (for example code that runs inside another framework's
+ * memory pool, under a capture that forbids allocation, or with the whole
+ * device already handed out): this call never calls cudaMalloc, cudaFree or
+ * any allocating library routine.  The paper has no counterpart; it exists
+ * for such callers.  The exact fixed-point path needs a scratch copy of x
+ * (8 bytes per state); here that scratch is a fixed device array compiled
+ * into the library (32 MiB, held by every GPU that loads the library until
+ * the process exits), so sectors above 4,194,272 states are rejected with
+ * ED_EINVAL.  Models whose couplings are not dyadic use the FP64 kernels,
+ * which need no scratch.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: two calls
+ * that overlap on the GPU (different streams, or different contexts)
+ * race and give wrong results.  x, y: device FP64, not overlapping,
+ * x 16-byte aligned; enqueued on `stream`. */
+ed_status ed_apply_H_noalloc(ed_ctx* ctx, const void* x, void* y, void* stream);
+
 /* Lanczos options / report (paper: H|psi> as the kernel of a Krylov
  * solver).  mode: ED_LZ_F64 plain FP64; ED_LZ_F32 FP32 storage with FP64
  * reductions; ED_LZ_MIXED FP32 Lanczos then FP64 restarted refinement until

@@ -18,6 +18,7 @@ from .ed import (  # noqa: E402,F401
     LanczosResult,
     Server,
     apply_H,
+    apply_H_noalloc,
     build_local_ops,
     build_sectors,
     lanczos_gf,
@@ -26,5 +27,5 @@ from .ed import (  # noqa: E402,F401
 )
 from ._lib import EDError  # noqa: E402,F401
 
-__all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "LanczosResult", "Server", "apply_H", "build_local_ops", "build_sectors", "lanczos_gf",
+__all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "LanczosResult", "Server", "apply_H", "apply_H_noalloc", "build_local_ops", "build_sectors", "lanczos_gf",
            "lanczos_ground", "random_vector", "EDError"]

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("ed_build_sectors", c_int, [P(ModelDesc), P(c_void_p)]),
     ("ed_build_local_ops", c_int, [c_void_p, c_int]),
     ("ed_apply_H", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    ("ed_apply_H_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("ed_lanczos_default_opts", None, [P(LanczosOpts)]),
     ("ed_lanczos_ground", c_int, [c_void_p, P(LanczosOpts), P(c_double), c_void_p, P(Report)]),
     ("ed_lanczos_gf", c_int, [c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_void_p, c_int, c_double,

@@ -14,6 +14,7 @@
 // stay resident in L2.
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "ed_internal.h"
 
@@ -580,9 +581,74 @@ ed_status apply_v3(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t 
   return r;
 }
 
+// ---------------------------------------------------------------- apply without allocation
+
+// Scratch of ed_apply_H_noalloc: a file-scope device array (one int for the
+// exponent of max|x|, then the 64-bit fixed-point copy of x).  Every GPU
+// that loads this library holds it until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+constexpr size_t kNoAllocHeader = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// device address of the scratch on the current device; the first call on a
+// device looks it up (cudaGetSymbolAddress) and caches it
+static ed_status noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("device %d outside the %d devices the scratch table covers", dev, kNoAllocMaxDevices);
+    return ED_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev, cudaGetErrorString(e));
+      return ED_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_ptr[dev];
+  return ED_OK;
+}
+
 }  // namespace edk
 
 using namespace edk;
+
+extern "C" ed_status ed_apply_H_noalloc(ed_ctx* c, const void* x, void* y, void* stream) {
+  if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }
+  if (!c->ops_built) { set_error("ed_build_local_ops has not been called"); return ED_EINVAL; }
+  if (c->D > 0 && (!x || !y)) { set_error("x or y is NULL"); return ED_EINVAL; }
+  const size_t need = kNoAllocHeader + (size_t)c->D * sizeof(long long);
+  if (c->dyadic && need > kNoAllocScratchBytes) {
+    set_error("ed_apply_H_noalloc: %lld states need %zu bytes of scratch, the static scratch holds %zu "
+              "(at most %zu states)", (long long)c->D, need, kNoAllocScratchBytes,
+              (kNoAllocScratchBytes - kNoAllocHeader) / sizeof(long long));
+    return ED_EINVAL;
+  }
+  const char* xb = (const char*)x;
+  const char* yb = (const char*)y;
+  if (c->D > 0 && xb < yb + c->D * 8 && yb < xb + c->D * 8) { set_error("x and y overlap"); return ED_EINVAL; }
+  if (!v3_usable(c, ED_F64, x)) {
+    set_error("ed_apply_H_noalloc needs the class-sorted kernels (16-byte aligned x, at most 4 value classes, "
+              "32 cross bonds and 65534 states per side charge)");
+    return ED_EUNSUPPORTED;
+  }
+  ED_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  ProfMarks pm;  // no profiling events here
+  if (!c->dyadic) return run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st, pm);
+  unsigned char* base = nullptr;
+  ED_TRY(noalloc_scratch(c->device, &base));
+  return apply_fixed(c, (const double*)x, (double*)y, (long long*)(base + kNoAllocHeader), (int*)base, st, pm);
+}
+
+
 
 extern "C" ed_status ed_profile_enable(ed_ctx* c, int enable) {
   if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }

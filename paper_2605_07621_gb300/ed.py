@@ -165,6 +165,16 @@ def apply_H(ctx: Context, x, y, stream=None):
     return y
 
 
+def apply_H_noalloc(ctx: Context, x, y, stream=None):
+    """y = H x (float64 CUDA tensors) without any device allocation (see ed_apply_H_noalloc)."""
+    import torch
+
+    _check_vec(ctx, x, "x", torch.float64)
+    _check_vec(ctx, y, "y", torch.float64)
+    L.check(L.load().ed_apply_H_noalloc(ctx.handle, _ptr(x), _ptr(y), _stream_handle(stream)))
+    return y
+
+
 def random_vector(ctx: Context, x, seed: int = 20260507, stream=None):
     import torch
 
