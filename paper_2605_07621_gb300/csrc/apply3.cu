@@ -32,6 +32,7 @@ struct P3 {
 
 struct PF32 {
   using S = float;
+  static constexpr bool kUniformCross = true;
   __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
   __device__ static float bw(const Dev3& t, int k) { return t.bond_w32[k]; }
   __device__ static float diagA(const Dev3& t, long long gA) { return t.A_d32[gA] + t.dc0_32; }
@@ -49,6 +50,7 @@ struct PF32 {
 };
 struct PF64 {
   using S = double;
+  static constexpr bool kUniformCross = true;
   __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
   __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
   __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
@@ -66,6 +68,7 @@ struct PF64 {
 };
 struct PI64 {
   using S = long long;
+  static constexpr bool kUniformCross = false;
   __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
   __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
   __device__ static long long diagA(const Dev3& t, long long gA) { return (long long)t.A_dI[gA] + t.dc0_I; }
@@ -384,21 +387,44 @@ __global__ void __launch_bounds__(kRowThreads, 2)
         unsigned dr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) dr[r] = r < nr ? (pa[r] ^ pb) : 0u;
-        for (int ib = 0; ib < t.n_ib; ++ib) {
-          const unsigned rm = t.ib_mask[ib];
-          unsigned any = 0;
+        if constexpr (Pol::kUniformCross) {
+          // floating point: loop over every bond with warp-uniform table
+          // indices (B site, bond, weight); only the validity predicate and
+          // the gather address vary across lanes; one FMA per valid bond
+          for (int ib = 0; ib < t.n_ib; ++ib) {
+            const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
+            unsigned km = t.ib_mask[ib];
+            while (km) {
+              const int k = __ffs(km) - 1;
+              km &= km - 1;
+              const S wk = Pol::bw(t, k);
+              const int ia = t.bond_ia[k];
 #pragma unroll
-          for (int r = 0; r < R; ++r) any |= dr[r] & rm;
-          if (!any) continue;
-          const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
+              for (int r = 0; r < R; ++r) {
+                const S* sp = src_row[r][ia];
+                if (((dr[r] >> k) & 1u) && sp) acc[r] += wk * __ldg(sp + mq);
+              }
+            }
+          }
+        } else {
+          // 64-bit integers: visit only each lane's valid bonds, so the
+          // multiply-adds are not spent on bonds that contribute nothing
+          for (int ib = 0; ib < t.n_ib; ++ib) {
+            const unsigned rm = t.ib_mask[ib];
+            unsigned any = 0;
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            unsigned dd = dr[r] & rm;
-            while (dd) {
-              const int k = __ffs(dd) - 1;
-              dd &= dd - 1;
-              const S* sp = src_row[r][t.bond_ia[k]];
-              if (sp) acc[r] += Pol::bw(t, k) * __ldg(sp + mq);
+            for (int r = 0; r < R; ++r) any |= dr[r] & rm;
+            if (!any) continue;
+            const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              unsigned dd = dr[r] & rm;
+              while (dd) {
+                const int k = __ffs(dd) - 1;
+                dd &= dd - 1;
+                const S* sp = src_row[r][t.bond_ia[k]];
+                if (sp) acc[r] += Pol::bw(t, k) * __ldg(sp + mq);
+              }
             }
           }
         }
@@ -528,14 +554,16 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
   long long se;
   constexpr int R = sizeof(typename Pol::S) == 4 ? 2 : 1;
   const size_t smem = v3_smem(c, sizeof(typename Pol::S), &se);
-  auto kern = k_row5<Pol, R>;
-  ED_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int sms = n_sms(c->device);
-  const long long* gs = R == 2 ? c->d_grp2_start : c->d_row_start;
-  const long long ng = R == 2 ? c->n_grp2 : c->n_rows;
-  const long long grid = std::min<long long>(ng, (long long)sms * 2);
   pm.mark(2, st);
-  kern<<<(unsigned)grid, kRowThreads, smem, st>>>(p, gs, ng, x, y, emax, se, c->d_err);
+  {
+    auto kern = k_row5<Pol, R>;
+    ED_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long* gs = R == 2 ? c->d_grp2_start : c->d_row_start;
+    const long long ng = R == 2 ? c->n_grp2 : c->n_rows;
+    const long long grid = std::min<long long>(ng, (long long)sms * 2);
+    kern<<<(unsigned)grid, kRowThreads, smem, st>>>(p, gs, ng, x, y, emax, se, c->d_err);
+  }
   ED_CUDA_TRY(cudaGetLastError());
   pm.mark(3, st);
   if (c->n_panel_items > 0) {

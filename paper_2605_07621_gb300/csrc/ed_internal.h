@@ -153,7 +153,10 @@ struct Dev3 {
   const uint2* B_col4;      // 4 x uint16 per element
   // cross bonds grouped by B site: bonds with B site ib are bits ib_mask[ib]
   int n_ib;
+  int n_ia;
   unsigned ib_mask[32];
+  unsigned ia_mask[32];     // bonds (bits) whose A site is ia
+  unsigned char bond_ib[32];
   unsigned char bond_ia[32];
   float bond_w32[32];
   double bond_w64[32];

@@ -203,11 +203,14 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
     c->cross_cls[k] = ci;
     t.cross_cls_mask[ci] |= 1u << k;
     t.ib_mask[c->cross[k].ib] |= 1u << k;
+    t.ia_mask[c->cross[k].ia] |= 1u << k;
     t.bond_ia[k] = (unsigned char)c->cross[k].ia;
+    t.bond_ib[k] = (unsigned char)c->cross[k].ib;
     t.bond_w64[k] = c->cross[k].coef;
     t.bond_w32[k] = (float)c->cross[k].coef;
   }
   t.n_ib = (int)c->crossB_bits.size();
+  t.n_ia = (int)c->crossA_bits.size();
   const DevDiagParams& dp = c->diag;
   t.vab_and = dp.vab_and;
   t.ncls_d = dp.ncls;
