@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--batch-n", type=int, default=512)
     p.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrival rate (requests/s)")
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
+    p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
     return p.parse_args()
 
 
@@ -57,6 +58,35 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def shard(n: int, rank: int, world: int):
+    """Instances handled by `rank` when n independent instances are spread
+    over `world` ranks (round robin; no data exchange between ranks)."""
+    return list(range(rank, n, world))
+
+
+def max_over_ranks(value: float, world: int, device: str = "cpu") -> float:
+    """Largest value over all ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device: str = "cpu") -> float:
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 def kernel_source_hash():
@@ -151,12 +181,15 @@ def cpu_baseline(model, budget_s: float = 12.0):
                       f"({t_keys:.1f} s to enumerate, not timed), all threads"}
 
 
-def batched_and_served(ed, n: int, rate: float, seed: int = 20260507):
-    """512 independent Hubbard instances: one batched Lanczos solve, then the
-    same instances as a Poisson stream of requests to the serving loop."""
+def batched_and_served(ed, n: int, rate: float, seed: int = 20260507, rank: int = 0, world: int = 1):
+    """512 independent Hubbard instances (this rank's share when several GPUs
+    run): one batched Lanczos solve, then the same instances as a Poisson
+    stream of requests to the serving loop."""
     import torch
 
-    models = W.batched_hubbard_instances(n, seed)
+    all_models = W.batched_hubbard_instances(n, seed)
+    models = [all_models[i] for i in shard(n, rank, world)]
+    n = len(models)
     t0 = time.perf_counter()
     b = ed.batch_create(models)
     t_create = time.perf_counter() - t0
@@ -205,6 +238,57 @@ def batched_and_served(ed, n: int, rate: float, seed: int = 20260507):
               "p99_ms": 1e3 * float(np.percentile(lat, 99)), "throughput_rps": n / wall,
               "max_slots": 512, "failed": int(st["failed"]), "max_abs_diff_vs_batched_e0": same}
     return batched, served
+
+
+def other_configs(ed):
+    """The other workloads: Heis16 (150 fixed steps), Hub12 (ground state FP64
+    and mixed, G on 2048 frequencies), Hub4x4 (H psi rates, ground state FP64
+    and mixed to 1e-10, G on 4096 frequencies with 400 steps, eta = 0.05)."""
+    import torch
+
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    ctx = ed.build_local_ops(ed.build_sectors(W.config_heis16()))
+    r, dt = timed(lambda: ed.lanczos_ground(ctx, mode="f64", max_iter=150, fixed_iter=True))
+    out["heis16"] = {"states": ctx.dim, "e0_150": r.e0, "seconds_150_steps": dt, "us_per_step": 1e6 * dt / 150}
+    for name, n_om, n_it in (("hub12", 2048, 300), ("hub4x4", 4096, 400)):
+        m = W.config_by_name(name)
+        ctx = ed.build_local_ops(ed.build_sectors(m))
+        rec = {"states": ctx.dim}
+        x = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+        ed.random_vector(ctx, x)
+        for dt_ in (torch.float64, torch.float32):
+            xx = x.to(dt_)
+            yy = torch.empty_like(xx)
+            ed.apply_H(ctx, xx, yy)
+            _, t1 = timed(lambda: [ed.apply_H(ctx, xx, yy) for _ in range(5)])
+            rec["hpsi_per_s_" + ("f64" if dt_ == torch.float64 else "f32")] = 5 / t1
+            del xx, yy
+        del x
+        for mode in ("f64", "mixed"):
+            r, t1 = timed(lambda: ed.lanczos_ground(ctx, mode=mode, tol=1e-12))
+            rec[f"e0_{mode}"] = r.e0
+            rec[f"time_to_e0_{mode}_s"] = t1
+            rec[f"iterations_{mode}"] = r.iterations
+        rec["mixed_vs_f64_rel"] = abs(rec["e0_mixed"] - rec["e0_f64"]) / abs(rec["e0_f64"])
+        psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+        r, t1 = timed(lambda: ed.lanczos_ground(ctx, mode="mixed", tol=1e-12, psi0=psi))
+        rec["ground_vector_s"] = t1
+        omega = np.linspace(-15.0, 15.0, n_om)
+        (G, co), t2 = timed(lambda: ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=n_it))
+        rec["gf"] = {"n_omega": n_om, "n_iter": n_it, "eta": 0.05, "seconds": t2,
+                     "sum_rule": co["particle"][0] + co["hole"][0], "max_im_G": float(G.imag.max())}
+        out[name] = rec
+        del psi, ctx
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -306,11 +390,7 @@ def main():
     stage_ms, n_prof = ctx.profile_read(reset=True)
     ctx.profile(False)
     stage_ms = stage_ms / max(n_prof, 1)
-    t_max = ms
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms, ws, device=str(dev))
     ms_per_step = t_max / args.steps
     value = ws * args.steps / (t_max / 1000.0)
 
@@ -346,7 +426,7 @@ def main():
         traffic = None
     # dominant kernel: the row pass (stage 2) -- reads every row of x once and
     # writes every element of y once, i.e. the algorithmic bytes of H|psi>
-    names = ["k_exp_max", "k_to_fixed", "k_row4", "k_panel3"]
+    names = ["k_exp_max", "k_to_fixed", "k_row5", "k_panel3"]
     dom = int(np.argmax(stage_ms))
     dom_ms = float(stage_ms[dom])
     achieved_dom = alg_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
@@ -396,12 +476,26 @@ def main():
         lanczos["speedup_mixed"] = lanczos["f64"]["seconds"] / lanczos["mixed"]["seconds"]
 
     batched = served = None
-    if rank == 0 and not args.no_batched:
+    if not args.no_batched:
         torch.cuda.empty_cache()
         try:
-            batched, served = batched_and_served(ed, args.batch_n, args.serve_rate)
+            batched, served = batched_and_served(ed, args.batch_n, args.serve_rate, rank=rank, world=ws)
+            # instances are sharded by rank: job time = slowest rank
+            t_solve = max_over_ranks(batched["solve_s"], ws, device=str(dev))
+            batched["instances_total"] = args.batch_n
+            batched["instances_per_s_job"] = args.batch_n / t_solve
+            batched["hpsi_per_s_job"] = sum_over_ranks(batched["hpsi_per_s_aggregate"] * batched["solve_s"], ws,
+                                                       device=str(dev)) / t_solve
         except Exception as exc:
             batched = {"error": str(exc)}
+
+    configs = None
+    if rank == 0 and not args.no_configs:
+        torch.cuda.empty_cache()
+        try:
+            configs = other_configs(ed)
+        except Exception as exc:
+            configs = {"error": str(exc)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -420,7 +514,7 @@ def main():
                            "setup_s": t_setup},
                 "gpu_launches": args.steps * (4 if args.dtype == "f64" else 2),
                 "roofline": roof, "clocks": clk, "e2e": e2e, "other_precision": other, "lanczos": lanczos,
-                "batched": batched, "serving": served, "cpu_baseline": cpu}
+                "batched": batched, "serving": served, "configs": configs, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -503,7 +503,11 @@ extern "C" ed_status ed_lanczos_gf(ed_ctx* c, const void* psi0, double e0, int s
     // free device memory; otherwise the plain three-term recurrence
     const int steps = (int)std::min<long long>(n_iter, n2);
     Basis B;
-    const bool ro = steps <= kMaxBasis && B.init(BASIS_SAME, sizeof(double), n2, steps + 1, free_device_bytes() / 2);
+    // (a partial basis would only re-orthogonalise the first steps, at O(j n)
+    // cost each, so it is used only when every step's vector fits)
+    const bool ro = steps <= kMaxBasis &&
+                    (size_t)(steps + 1) * (size_t)n2 * sizeof(double) <= free_device_bytes() / 2 &&
+                    B.init(BASIS_SAME, sizeof(double), n2, steps + 1, free_device_bytes() / 2) && B.cap >= steps + 1;
     RunOut r;
     ED_TRY(lz_run<double>(c2, st, bufs, phi, steps, 0.0, 1, true, ro, ro ? &B : nullptr, r));
     ED_CUDA_TRY(cudaStreamSynchronize(st));
