@@ -47,17 +47,19 @@ def heis16():
 
 
 def hub12():
+    """Hub12 ground state and the Lanczos coefficients of c^dag_{0 up} psi0 and
+    c_{0 up} psi0 (500 steps each, full reorthogonalisation).  G(omega) at any
+    eta and any truncation length follows from them."""
     m = W.config_hub12()
     keys = oracle.sector_keys(m)
     t = time.time()
     e0, psi, _ = oracle.ground_state(m, keys, n_iter=300, tol=1e-14)
-    omega = np.linspace(-15.0, 15.0, 2048)
-    G, co = oracle.green_function(m, psi, e0, omega, 0.05, site=0, spin=0, n_iter=300, keys=keys, reorth=True,
+    G, co = oracle.green_function(m, psi, e0, [0.0], 0.05, site=0, spin=0, n_iter=500, keys=keys, reorth=True,
                                   return_coeffs=True)
-    return {"config": "hub12", "e0": e0, "eta": 0.05, "n_iter": 300, "omega": [-15.0, 15.0, 2048],
-            "G_re": G.real.tolist(), "G_im": G.imag.tolist(),
-            "w_particle": co["particle"][0], "w_hole": co["hole"][0],
-            "a_particle_0_29": co["particle"][1][:30].tolist(), "b_particle_1_30": co["particle"][2][:30].tolist(),
+    return {"config": "hub12", "e0": e0, "site": 0, "spin": 0, "n_iter": 500,
+            "w_particle": co["particle"][0], "a_particle": co["particle"][1].tolist(),
+            "b_particle": co["particle"][2].tolist(),
+            "w_hole": co["hole"][0], "a_hole": co["hole"][1].tolist(), "b_hole": co["hole"][2].tolist(),
             "seconds": time.time() - t}
 
 

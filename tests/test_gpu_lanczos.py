@@ -110,31 +110,49 @@ def test_cut_independence_j1j2_4x4(ed):
     assert max(es) - min(es) < 1e-10 * abs(es[0])
 
 
+def _cf_green(g, omega, eta, m):
+    """G(omega + i eta) from the first m oracle coefficients of both runs."""
+    import oracle
+
+    z = np.asarray(omega) + 1j * eta
+    ap, bp = np.array(g["a_particle"][:m]), np.array(g["b_particle"][: m - 1])
+    ah, bh = np.array(g["a_hole"][:m]), np.array(g["b_hole"][: m - 1])
+    return (oracle.continued_fraction(z + g["e0"], g["w_particle"], ap, bp)
+            - oracle.continued_fraction(g["e0"] - z, g["w_hole"], ah, bh))
+
+
 def test_hub12_green_function(ed):
-    """Hub12 G_00: the first Lanczos coefficients of the particle run and the
-    weights ||c^dag psi0||^2, ||c psi0||^2 against the oracle.  Later
-    coefficients are ill-conditioned functions of the start vector (roundoff
-    differences of H psi grow after ~12 steps even with full
-    reorthogonalisation on both sides), so they are not compared."""
+    """Hub12 G_00(omega), 2048 frequencies on [-15, 15], 300 Lanczos steps.
+
+    The oracle's coefficients (500 steps, full reorthogonalisation) are
+    stored; G follows from any prefix.  At eta = 0.5 a 300-step continued
+    fraction is converged and the GPU must agree to 1e-9.  At eta = 0.05 the
+    300-step fraction is itself only accurate to its truncation error (the
+    oracle's 300- and 500-step values differ by ~1e-3) and later Lanczos
+    coefficients are ill-conditioned, so the check there is agreement within
+    twice that truncation spread.  The first coefficients and the weights are
+    well conditioned and are compared tightly."""
     import torch
 
     g = _gold("hub12.json")
-    m = W.config_hub12()
-    ctx = _ctx(ed, m)
+    ctx = _ctx(ed, W.config_hub12())
     psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
     r = ed.lanczos_ground(ctx, mode="f64", psi0=psi, tol=1e-14)
     assert abs(r.e0 - g["e0"]) <= 1e-10 * abs(g["e0"])
-    lo, hi, n = g["omega"]
-    omega = np.linspace(lo, hi, n)
-    G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, g["eta"], site=0, spin=0, n_iter=g["n_iter"])
+    omega = np.linspace(-15.0, 15.0, 2048)
+    G5, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.5, site=0, spin=0, n_iter=300)
     assert abs(co["particle"][0] - g["w_particle"]) < 1e-9
     assert abs(co["hole"][0] - g["w_hole"]) < 1e-9
     assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-9
-    ap, bp = co["particle"][1], co["particle"][2]
-    assert np.abs(ap[:10] - np.array(g["a_particle_0_29"][:10])).max() < 1e-8
-    assert np.abs(bp[:10] - np.array(g["b_particle_1_30"][:10])).max() < 1e-8
-    # causality of the retarded function: Im G <= 0 everywhere
-    assert G.imag.max() <= 0.0
+    assert np.abs(co["particle"][1][:10] - np.array(g["a_particle"][:10])).max() < 1e-8
+    assert np.abs(co["particle"][2][:10] - np.array(g["b_particle"][:10])).max() < 1e-8
+    ref5 = _cf_green(g, omega, 0.5, 300)
+    assert np.abs(G5 - ref5).max() <= 1e-9 * np.abs(ref5).max()
+    G05, _ = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=300)
+    ref300 = _cf_green(g, omega, 0.05, 300)
+    spread = np.abs(ref300 - _cf_green(g, omega, 0.05, 500)).max()
+    assert np.abs(G05 - ref300).max() <= 2.0 * spread
+    assert G05.imag.max() <= 0.0  # retarded: -Im G / pi is a spectral density
 
 
 @pytest.mark.parametrize("spin,site", [(0, 0), (1, 3)])
