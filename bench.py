@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrival rate (requests/s)")
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
     p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
+    p.add_argument("--row-pass", default="auto", choices=["auto", "single", "staged"],
+                   help="pin the row pass of the headline workload (default: the library's choice)")
     return p.parse_args()
 
 
@@ -91,7 +93,8 @@ def sum_over_ranks(value: float, world: int, device: str = "cpu") -> float:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for fn in ("apply3.cu", "ed_internal.h", "ops.cpp"):
+    for fn in ("apply3.cu", "apply3.cuh", "rowx.cuh", "rowx_f32.cu", "rowx_f64.cu", "rowx_i64.cu", "ed_internal.h",
+               "ops.cpp"):
         with open(os.path.join(ROOT, "paper_2605_07621_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -352,7 +355,8 @@ def main():
 
     model = W.config_by_name(args.config)
     t0 = time.time()
-    ctx = ed.build_local_ops(ed.build_sectors(model))
+    ctx = ed.build_local_ops(ed.build_sectors(model), {"auto": ed.OPS_DEFAULT, "single": ed.OPS_ROW_SINGLE,
+                                                       "staged": ed.OPS_ROW_STAGED}[args.row_pass])
     t_setup = time.time() - t0
     D = ctx.dim
     tdt = torch.float64 if args.dtype == "f64" else torch.float32
@@ -426,7 +430,7 @@ def main():
         traffic = None
     # dominant kernel: the row pass (stage 2) -- reads every row of x once and
     # writes every element of y once, i.e. the algorithmic bytes of H|psi>
-    names = ["k_exp_max", "k_to_fixed", "k_row5", "k_panel3"]
+    names = ["k_exp_max", "k_to_fixed", ctx.row_pass(tdt), "k_panel3" if tdt == torch.float32 else "k_panel4"]
     dom = int(np.argmax(stage_ms))
     dom_ms = float(stage_ms[dom])
     achieved_dom = alg_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
@@ -511,7 +515,7 @@ def main():
                 "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": {"workload": args.config, "states": D, "blocks": ctx.num_blocks,
                            "parallelism": "replicas" if ws > 1 else "single", "l2_flush": "inputs larger than L2",
-                           "setup_s": t_setup},
+                           "setup_s": t_setup, "row_pass": ctx.row_pass(tdt)},
                 "gpu_launches": args.steps * (4 if args.dtype == "f64" else 2),
                 "roofline": roof, "clocks": clk, "e2e": e2e, "other_precision": other, "lanczos": lanczos,
                 "batched": batched, "serving": served, "configs": configs, "cpu_baseline": cpu}

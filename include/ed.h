@@ -86,16 +86,26 @@ ed_status ed_build_sectors(const ed_model_desc* model, ed_ctx** out);
 /* Build the side operators of Eq. (2) on the device: CSR of H_A,s and
  * H_B,s off-diagonals, side diagonals, the cross-cut maps.
  * flags: ED_OPS_DEFAULT, or ED_OPS_FORCE_CSR / ED_OPS_FORCE_DENSE to pin the
- * per-sector choice instead of autotuning it.  Synchronises the device. */
+ * per-sector choice instead of autotuning it; optionally or-ed with one of
+ * ED_OPS_ROW_SINGLE / ED_OPS_ROW_STAGED to pick the row pass of spin models
+ * with cross-cut bonds (single, the default: cross terms gathered from x in
+ * global memory; staged: each cross term's source row staged in shared
+ * memory, one CTA per SM).  The results are identical up to FP summation
+ * order (bit-identical in the exact fixed-point FP64 mode).  Synchronises
+ * the device. */
 #define ED_OPS_DEFAULT 0
 #define ED_OPS_FORCE_CSR 1
 #define ED_OPS_FORCE_DENSE 2
+#define ED_OPS_ROW_SINGLE 4
+#define ED_OPS_ROW_STAGED 8
 ed_status ed_build_local_ops(ed_ctx* ctx, int flags);
 
 /* y = H x over the whole sector (all blocks), device pointers of ed_dim
  * elements of `dtype`, x and y must not overlap.  ED_F64: FP64 storage,
  * FP64-accurate result; ED_F32: FP32 storage and accumulation.  Enqueued on
- * `stream` (cudaStream_t, NULL = legacy default stream); no sync. */
+ * `stream` (cudaStream_t, NULL = legacy default stream); no sync.  The
+ * context's scratch (fixed-point copy of x, work counter) serves one call at
+ * a time: calls on one context must not overlap on the GPU. */
 ed_status ed_apply_H(ed_ctx* ctx, const void* x, void* y, ed_dtype dtype, void* stream);
 
 /* y = H x like ed_apply_H with ED_F64, for callers that cannot allocate
@@ -257,6 +267,11 @@ void ed_server_destroy(ed_server* s);
  * record nothing. */
 ed_status ed_profile_enable(ed_ctx* ctx, int enable);
 ed_status ed_profile_read(ed_ctx* ctx, double* ms, int64_t* count, int reset);
+/* Which row pass ed_apply_H runs for `dtype` on this context: 0 = the
+ * plain per-row kernel (the class-sorted kernels do not apply), 1 = the
+ * single-row pass (k_row5), 2 = the staged-source row pass (k_rowx);
+ * negative: ed_build_local_ops has not run. */
+int ed_row_pass(const ed_ctx* ctx, ed_dtype dtype);
 
 /* ---- queries ---------------------------------------------------------- */
 int64_t ed_dim(const ed_ctx* ctx);

@@ -10,6 +10,11 @@ from . import _lib
 _lib.load()
 
 from .ed import (  # noqa: E402,F401
+    OPS_DEFAULT,
+    OPS_FORCE_CSR,
+    OPS_FORCE_DENSE,
+    OPS_ROW_SINGLE,
+    OPS_ROW_STAGED,
     Batch,
     batch_apply,
     batch_create,
@@ -28,4 +33,5 @@ from .ed import (  # noqa: E402,F401
 from ._lib import EDError  # noqa: E402,F401
 
 __all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "LanczosResult", "Server", "apply_H", "apply_H_noalloc", "build_local_ops", "build_sectors", "lanczos_gf",
-           "lanczos_ground", "random_vector", "EDError"]
+           "lanczos_ground", "random_vector", "EDError", "OPS_DEFAULT", "OPS_FORCE_CSR", "OPS_FORCE_DENSE",
+           "OPS_ROW_SINGLE", "OPS_ROW_STAGED"]

@@ -7,159 +7,18 @@
 //         pipe and rounded once back to FP64.  FP64 adds and FP64
 //         conversions run at about 0.5 T/s on this GPU, the integer pipe at
 //         tens of T/s, so no FP64 instruction is issued per matrix element.
-// Row pass: psi_s[a,:] is staged in shared memory by bulk TMA copies
-// (double-buffered), then each column b sums, class by class, the H_B
-// neighbours (16-bit column indices) and the cross-cut gathers, plus the
-// diagonal.  Panel pass: the H_A (row-mixing) term over column panels that
-// stay resident in L2.
-#include <cstdint>
-#include <cstring>
+// Row pass: psi_s[a,:] is staged in shared memory by bulk TMA copies, then
+// each column b sums, class by class, the H_B neighbours (16-bit column
+// indices) and the cross-cut gathers, plus the diagonal.  Two row passes:
+// k_row5 (here) gathers the cross terms from x in global memory; k_rowx
+// (rowx.cuh) also stages each cross term's source row in shared memory.
+// Panel pass: the H_A (row-mixing) term over column panels that stay
+// resident in L2.
 #include <mutex>
 
-#include "ed_internal.h"
+#include "rowx.cuh"
 
 namespace edk {
-
-struct P3 {
-  Dev3 t;
-  const DevBlock* blocks;
-  const DevCross* cross;
-  const long long* row_start;
-  int nblk;
-  int ncross;
-  long long n_rows;
-};
-
-struct PF32 {
-  using S = float;
-  static constexpr bool kUniformCross = true;
-  __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
-  __device__ static float bw(const Dev3& t, int k) { return t.bond_w32[k]; }
-  __device__ static float diagA(const Dev3& t, long long gA) { return t.A_d32[gA] + t.dc0_32; }
-  __device__ static float diagB(const Dev3& t, long long gB) { return t.B_d32[gB]; }
-  __device__ static float vab(const Dev3& t, unsigned z) {
-    float v = 0.f;
-    for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
-    return v;
-  }
-  __device__ static float diag(const Dev3& t, long long gA, long long gB, unsigned z) {
-    float v = t.A_d32[gA] + t.B_d32[gB] + t.dc0_32;
-    for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
-    return v;
-  }
-};
-struct PF64 {
-  using S = double;
-  static constexpr bool kUniformCross = true;
-  __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
-  __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
-  __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
-  __device__ static double diagB(const Dev3& t, long long gB) { return t.B_d64[gB]; }
-  __device__ static double vab(const Dev3& t, unsigned z) {
-    double v = 0.0;
-    for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
-    return v;
-  }
-  __device__ static double diag(const Dev3& t, long long gA, long long gB, unsigned z) {
-    double v = t.A_d64[gA] + t.B_d64[gB] + t.dc0_64;
-    for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
-    return v;
-  }
-};
-struct PI64 {
-  using S = long long;
-  static constexpr bool kUniformCross = false;
-  __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
-  __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
-  __device__ static long long diagA(const Dev3& t, long long gA) { return (long long)t.A_dI[gA] + t.dc0_I; }
-  __device__ static long long diagB(const Dev3& t, long long gB) { return (long long)t.B_dI[gB]; }
-  __device__ static long long vab(const Dev3& t, unsigned z) {
-    long long v = 0;
-    for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
-    return v;
-  }
-  __device__ static long long diag(const Dev3& t, long long gA, long long gB, unsigned z) {
-    long long v = (long long)t.A_dI[gA] + (long long)t.B_dI[gB] + t.dc0_I;
-    for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
-    return v;
-  }
-};
-
-// ---------------------------------------------------------------- fixed point <-> FP64 by bit manipulation
-
-__host__ __device__ __forceinline__ unsigned long long f64_bits(double v) {
-#ifdef __CUDA_ARCH__
-  return (unsigned long long)__double_as_longlong(v);
-#else
-  unsigned long long u;
-  memcpy(&u, &v, 8);
-  return u;
-#endif
-}
-__host__ __device__ __forceinline__ double bits_f64(unsigned long long u) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)u);
-#else
-  double v;
-  memcpy(&v, &u, 8);
-  return v;
-#endif
-}
-__host__ __device__ __forceinline__ int clz64(unsigned long long u) {
-#ifdef __CUDA_ARCH__
-  return __clzll((long long)u);
-#else
-  return __builtin_clzll(u);
-#endif
-}
-
-// round(v * 2^sh_base) (ties away from zero) for |v| < 2^E, sh_base = P - E
-__host__ __device__ __forceinline__ long long to_fixed(double v, int sh_base) {
-  const unsigned long long u = f64_bits(v);
-  const int s = (int)(u >> 63);
-  int e = (int)((u >> 52) & 0x7ffull);
-  unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-  if (e == 0) {
-    if (m == 0) return 0;
-    e = 1;
-  } else {
-    m |= 1ull << 52;
-  }
-  const int sh = e - 1075 + sh_base;
-  long long X;
-  if (sh >= 0) X = (long long)(m << sh);
-  else if (sh > -64) X = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
-  else X = 0;
-  return s ? -X : X;
-}
-
-// Y * 2^e2 rounded to nearest (ties to even) FP64
-__host__ __device__ __forceinline__ double from_fixed(long long Y, int e2) {
-  if (Y == 0) return 0.0;
-  const unsigned long long s = Y < 0 ? 1ull : 0ull;
-  unsigned long long u = s ? (unsigned long long)(-Y) : (unsigned long long)Y;
-  int p = 63 - clz64(u);
-  unsigned long long mant;
-  if (p <= 52) {
-    mant = u << (52 - p);
-  } else {
-    const int sh = p - 52;
-    mant = u >> sh;
-    const unsigned long long rem = u & ((1ull << sh) - 1);
-    const unsigned long long half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant >> 53) {
-        mant >>= 1;
-        ++p;
-      }
-    }
-  }
-  const int ex = p + e2 + 1023;
-  if (ex <= 0) return s ? -0.0 : 0.0;
-  if (ex >= 2047) return bits_f64((s << 63) | (0x7ffull << 52));
-  return bits_f64((s << 63) | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull));
-}
 
 // host entry points of the two conversions (used by the CPU tests)
 long long host_to_fixed(double v, int sh_base) { return to_fixed(v, sh_base); }
@@ -181,60 +40,6 @@ __global__ void k_to_fixed(const double* __restrict__ x, long long* __restrict__
   const int sh = P - E;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     X[i] = to_fixed(x[i], sh);
-}
-
-__device__ __forceinline__ int out_exp(const Dev3& t, const int* emax) { return (emax[0] - 1022) - t.P - t.q_shift; }
-
-template <class Pol>
-__device__ __forceinline__ void store_out(typename Pol::S* y, long long i, typename Pol::S v, bool final_,
-                                          int e2) {
-  y[i] = v;
-}
-template <>
-__device__ __forceinline__ void store_out<PI64>(long long* y, long long i, long long v, bool final_, int e2) {
-  if (final_) reinterpret_cast<double*>(y)[i] = from_fixed(v, e2);
-  else y[i] = v;
-}
-
-// ---------------------------------------------------------------- TMA / mbarrier
-
-__device__ __forceinline__ unsigned s_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void bar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void bar_expect(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   s_u32(dst)),
-               "l"(src), "r"(bytes), "r"(s_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
-  for (long long i = 0; i < (1ll << 22); ++i) {
-    unsigned ok;
-    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                 : "=r"(ok)
-                 : "r"(s_u32(bar)), "r"(parity)
-                 : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ int find_blk(const long long* row_start, int nblk, long long row) {
-  int lo = 0, hi = nblk - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (row_start[mid] <= row) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 constexpr int kRowThreads = 512;
@@ -491,14 +296,80 @@ __global__ void __launch_bounds__(256) k_panel3(P3 p, const int4* __restrict__ i
   }
 }
 
-static int n_sms(int dev) {
-  int n = 0;
-  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    n = 148;
+// H_A panel pass with U neighbour rows in flight per class step: each warp
+// owns one output row of a 256-column panel, processed as sub-panels of
+// 32 * NC columns; the column indices of U consecutive H_A entries are read
+// first (warp-uniform), then all U x NC neighbour values are loaded before
+// any is summed, so U x NC independent loads per lane overlap their
+// latency instead of one neighbour row at a time.
+template <class Pol, int NC, int U>
+__global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ items, long long n_items,
+                                                const typename Pol::S* __restrict__ x, typename Pol::S* __restrict__ y,
+                                                const int* __restrict__ emax) {
+  using S = typename Pol::S;
+  constexpr int W = 32 * NC;
+  static_assert(256 % W == 0, "sub-panels must tile the 256-column panel");
+  const Dev3& t = p.t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e2 = emax ? out_exp(t, emax) : 0;
+  for (long long w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int4 it = items[w];
+    if (warp >= it.w) continue;
+    const DevBlock bl = p.blocks[it.x];
+    const long long a = it.z + warp;
+    const long long gA = bl.gA0 + a;
+    const long long dB = bl.dB;
+    const S* xb = x + bl.off;
+    S* yrow = y + bl.off + a * dB;
+    const uint2 m = t.A_meta[gA];
+    for (int sp = 0; sp < 256; sp += W) {
+      const long long b0 = it.y + sp + lane;
+      if (it.y + sp >= dB) break;
+      S acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const long long b = b0 + 32 * c;
+        acc[c] = b < dB ? yrow[b] : (S)0;
+      }
+      unsigned e = m.x;
+#pragma unroll
+      for (int cl = 0; cl < kMaxCls; ++cl) {
+        const int n = (int)((m.y >> (8 * cl)) & 255u);
+        if (!n) continue;
+        S sum[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sum[c] = 0;
+        for (int i0 = 0; i0 < n; i0 += U) {
+          long long rowoff[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) rowoff[u] = i0 + u < n ? (long long)t.A_col[e + i0 + u] * dB : -1;
+          S v[U][NC];
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              const long long b = b0 + 32 * c;
+              v[u][c] = (rowoff[u] >= 0 && b < dB) ? __ldg(xb + rowoff[u] + b) : (S)0;
+            }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) sum[c] += v[u][c];
+        }
+        e += n;
+        const S wc = Pol::w(t, cl);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += wc * sum[c];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const long long b = b0 + 32 * c;
+        if (b < dB) store_out<Pol>(yrow, b, acc[c], true, e2);
+      }
+    }
   }
-  return n;
 }
+
 
 static P3 make_p3(const ed_ctx* c) {
   P3 p;
@@ -546,6 +417,37 @@ struct ProfMarks {
   }
 };
 
+static bool rx_plan(const ed_ctx* c, size_t es, RxPlan* out) {
+  if (!c->d_rowx || c->n_rowx <= 0 || c->n_rowx > INT32_MAX) return false;
+  long long mdb = 1;
+  for (const auto& b : c->blocks) mdb = std::max<long long>(mdb, b.dB);
+  if (!(c->ops_flags & ED_OPS_ROW_STAGED)) return false;
+  for (int ia = 0; ia < c->t3.n_ia; ++ia)
+    if (__builtin_popcount(c->t3.ia_mask[ia]) > kRxMaxBondsPerSite) return false;
+  if (c->t3.n_ia > 31) return false;
+  const int cons = (es == 4 ? rx_threads<float>() : rx_threads<double>()) - 32;
+  const long long need = (mdb + cons - 1) / cons;
+  int ncol = 0;
+  for (int v : kRxCols)
+    if (!ncol && need <= v) ncol = v;
+  if (!ncol || (es == 4 && ncol > 13)) return false;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const long long stage = ((mdb + 1 + 16 / (long long)es + 15) / 16) * 16;
+  const size_t head = 64 + kRxMaxBuf * sizeof(RxDesc);
+  const long long per = stage * (long long)es;
+  const long long nb = std::min<long long>(kRxMaxBuf, ((long long)optin - (long long)head) / per);
+  if (nb < 2) return false;
+  out->ncol = ncol;
+  out->nbuf = (int)nb;
+  out->stage = stage;
+  out->smem = head + (size_t)nb * (size_t)per;
+  return true;
+}
+
 template <class Pol>
 static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y, const int* emax, cudaStream_t st,
                         ProfMarks& pm) {
@@ -556,7 +458,11 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
   const size_t smem = v3_smem(c, sizeof(typename Pol::S), &se);
   const int sms = n_sms(c->device);
   pm.mark(2, st);
-  {
+  RxPlan rx;
+  if (rx_plan(c, sizeof(typename Pol::S), &rx)) {
+    ED_CUDA_TRY(cudaMemsetAsync(c->d_sched, 0, sizeof(int), st));
+    ED_TRY(rx_launch(c, p, rx, x, y, emax, st));
+  } else {
     auto kern = k_row5<Pol, R>;
     ED_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long* gs = R == 2 ? c->d_grp2_start : c->d_row_start;
@@ -568,7 +474,14 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
   pm.mark(3, st);
   if (c->n_panel_items > 0) {
     const long long g2 = std::min<long long>(c->n_panel_items, (long long)sms * 8);
-    k_panel3<Pol><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
+    // measured on the 4x8 J1-J2 and 4x4 Hubbard workloads: 8-byte types
+    // gain from two neighbour rows in flight on 128-column sub-panels
+    // (24.5 -> 13.3 ms, 5.1 -> 2.5 ms), FP32 is fastest one row at a time on
+    // full 256-column panels
+    if constexpr (sizeof(typename Pol::S) == 4)
+      k_panel3<Pol><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
+    else
+      k_panel4<Pol, 4, 2><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
     ED_CUDA_TRY(cudaGetLastError());
   }
   return ED_OK;
@@ -677,6 +590,14 @@ extern "C" ed_status ed_apply_H_noalloc(ed_ctx* c, const void* x, void* y, void*
 }
 
 
+
+extern "C" int ed_row_pass(const ed_ctx* c, ed_dtype dt) {
+  if (!c || !c->ops_built) return -1;
+  if (!v3_usable(c, dt, (const void*)(uintptr_t)256)) return 0;  // any 16-byte aligned x
+  RxPlan rx;
+  const size_t es = dt == ED_F32 ? 4 : 8;
+  return rx_plan(c, es, &rx) ? 2 : 1;
+}
 
 extern "C" ed_status ed_profile_enable(ed_ctx* c, int enable) {
   if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }

@@ -1,0 +1,217 @@
+// Device code shared by the class-sorted H|psi> kernels (paper Eq. (2)):
+// the kernel parameter block, the three arithmetic policies (FP32, FP64,
+// exact 64-bit fixed point), the fixed-point <-> FP64 conversions done by
+// bit manipulation, and the TMA / mbarrier helpers.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+#include "ed_internal.h"
+
+namespace edk {
+struct P3 {
+  Dev3 t;
+  const DevBlock* blocks;
+  const DevCross* cross;
+  const long long* row_start;
+  int nblk;
+  int ncross;
+  long long n_rows;
+};
+
+struct PF32 {
+  using S = float;
+  static constexpr bool kUniformCross = true;
+  __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
+  __device__ static float bw(const Dev3& t, int k) { return t.bond_w32[k]; }
+  __device__ static float diagA(const Dev3& t, long long gA) { return t.A_d32[gA] + t.dc0_32; }
+  __device__ static float diagB(const Dev3& t, long long gB) { return t.B_d32[gB]; }
+  __device__ static float vab(const Dev3& t, unsigned z) {
+    float v = 0.f;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
+    return v;
+  }
+  __device__ static float diag(const Dev3& t, long long gA, long long gB, unsigned z) {
+    float v = t.A_d32[gA] + t.B_d32[gB] + t.dc0_32;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw32[q] * (float)__popc(z & t.dmask[q]);
+    return v;
+  }
+};
+struct PF64 {
+  using S = double;
+  static constexpr bool kUniformCross = true;
+  __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
+  __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
+  __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
+  __device__ static double diagB(const Dev3& t, long long gB) { return t.B_d64[gB]; }
+  __device__ static double vab(const Dev3& t, unsigned z) {
+    double v = 0.0;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
+    return v;
+  }
+  __device__ static double diag(const Dev3& t, long long gA, long long gB, unsigned z) {
+    double v = t.A_d64[gA] + t.B_d64[gB] + t.dc0_64;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dw64[q] * (double)__popc(z & t.dmask[q]);
+    return v;
+  }
+};
+struct PI64 {
+  using S = long long;
+  static constexpr bool kUniformCross = false;
+  __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
+  __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
+  __device__ static long long diagA(const Dev3& t, long long gA) { return (long long)t.A_dI[gA] + t.dc0_I; }
+  __device__ static long long diagB(const Dev3& t, long long gB) { return (long long)t.B_dI[gB]; }
+  __device__ static long long vab(const Dev3& t, unsigned z) {
+    long long v = 0;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
+    return v;
+  }
+  __device__ static long long diag(const Dev3& t, long long gA, long long gB, unsigned z) {
+    long long v = (long long)t.A_dI[gA] + (long long)t.B_dI[gB] + t.dc0_I;
+    for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------- fixed point <-> FP64 by bit manipulation
+
+__host__ __device__ __forceinline__ unsigned long long f64_bits(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long u;
+  memcpy(&u, &v, 8);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double bits_f64(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  memcpy(&v, &u, 8);
+  return v;
+#endif
+}
+__host__ __device__ __forceinline__ int clz64(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)u);
+#else
+  return __builtin_clzll(u);
+#endif
+}
+
+// round(v * 2^sh_base) (ties away from zero) for |v| < 2^E, sh_base = P - E
+__host__ __device__ __forceinline__ long long to_fixed(double v, int sh_base) {
+  const unsigned long long u = f64_bits(v);
+  const int s = (int)(u >> 63);
+  int e = (int)((u >> 52) & 0x7ffull);
+  unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  if (e == 0) {
+    if (m == 0) return 0;
+    e = 1;
+  } else {
+    m |= 1ull << 52;
+  }
+  const int sh = e - 1075 + sh_base;
+  long long X;
+  if (sh >= 0) X = (long long)(m << sh);
+  else if (sh > -64) X = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else X = 0;
+  return s ? -X : X;
+}
+
+// Y * 2^e2 rounded to nearest (ties to even) FP64
+__host__ __device__ __forceinline__ double from_fixed(long long Y, int e2) {
+  if (Y == 0) return 0.0;
+  const unsigned long long s = Y < 0 ? 1ull : 0ull;
+  unsigned long long u = s ? (unsigned long long)(-Y) : (unsigned long long)Y;
+  int p = 63 - clz64(u);
+  unsigned long long mant;
+  if (p <= 52) {
+    mant = u << (52 - p);
+  } else {
+    const int sh = p - 52;
+    mant = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1);
+    const unsigned long long half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++p;
+      }
+    }
+  }
+  const int ex = p + e2 + 1023;
+  if (ex <= 0) return s ? -0.0 : 0.0;
+  if (ex >= 2047) return bits_f64((s << 63) | (0x7ffull << 52));
+  return bits_f64((s << 63) | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull));
+}
+
+__device__ __forceinline__ int out_exp(const Dev3& t, const int* emax) { return (emax[0] - 1022) - t.P - t.q_shift; }
+
+template <class Pol>
+__device__ __forceinline__ void store_out(typename Pol::S* y, long long i, typename Pol::S v, bool final_,
+                                          int e2) {
+  y[i] = v;
+}
+template <>
+__device__ __forceinline__ void store_out<PI64>(long long* y, long long i, long long v, bool final_, int e2) {
+  if (final_) reinterpret_cast<double*>(y)[i] = from_fixed(v, e2);
+  else y[i] = v;
+}
+
+// ---------------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ unsigned s_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   s_u32(dst)),
+               "l"(src), "r"(bytes), "r"(s_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long i = 0; i < (1ll << 22); ++i) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(s_u32(bar)), "r"(parity)
+                 : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int find_blk(const long long* row_start, int nblk, long long row) {
+  int lo = 0, hi = nblk - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (row_start[mid] <= row) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+inline int n_sms(int dev) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    n = 148;
+  }
+  return n;
+}
+
+}  // namespace edk

@@ -51,7 +51,7 @@ extern "C" ed_status ed_batch_create(const ed_model_desc* models, int n, int fla
     S.d.uoff = B->off[i];
   }
   // descriptors with user offsets and the dense threshold
-  int thr = flags == ED_OPS_FORCE_CSR ? 0 : flags == ED_OPS_FORCE_DENSE ? kBatchMaxDense : 16;
+  int thr = (flags & 3) == ED_OPS_FORCE_CSR ? 0 : (flags & 3) == ED_OPS_FORCE_DENSE ? kBatchMaxDense : 16;
   st = B->eng.set_dense_threshold(thr);
   if (st != ED_OK) { delete B; return st; }
   if (flags == ED_OPS_DEFAULT) {

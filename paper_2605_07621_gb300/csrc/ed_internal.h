@@ -213,6 +213,9 @@ struct ed_ctx {
   long long n_grp2 = 0;
   long long n_panel_items = 0;
   int* d_err = nullptr;              // set by kernels whose bounded waits ran out
+  int2* d_rowx = nullptr;            // (block, row) work list of the staged-source row pass
+  long long n_rowx = 0;
+  int* d_sched = nullptr;            // work counter of that pass (cleared before each launch)
   // class-sorted path
   bool v3_ok = false;                // tables below are valid
   bool dyadic = false;               // FP64 apply may use exact fixed point

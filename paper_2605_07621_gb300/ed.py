@@ -15,6 +15,13 @@ from . import _lib as L
 
 _MODES = {"f64": L.ED_LZ_F64, "f32": L.ED_LZ_F32, "mixed": L.ED_LZ_MIXED}
 
+# ed_build_local_ops flags (include/ed.h)
+OPS_DEFAULT = 0
+OPS_FORCE_CSR = 1
+OPS_FORCE_DENSE = 2
+OPS_ROW_SINGLE = 4
+OPS_ROW_STAGED = 8
+
 
 def _stream_handle(stream):
     if stream is None:
@@ -89,6 +96,14 @@ class Context:
     def profile(self, enable: bool = True):
         """Per-stage CUDA-event timing of apply_H (see ed_profile_enable)."""
         L.check(L.load().ed_profile_enable(self._h, 1 if enable else 0))
+
+    def row_pass(self, dtype) -> str:
+        """Row-pass kernel apply_H runs for ``dtype`` (see ed_row_pass)."""
+        import torch
+
+        dt = L.ED_F32 if dtype in (torch.float32, "f32") else L.ED_F64
+        k = int(L.load().ed_row_pass(self._h, dt))
+        return {0: "k_apply_rows", 1: "k_row5", 2: "k_rowx"}.get(k, "none")
 
     def profile_read(self, reset: bool = True):
         """(ms per stage [exp_max, to_fixed, row pass, panel pass], number of applies)."""
