@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrival rate (requests/s)")
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
     p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
-    p.add_argument("--row-pass", default="auto", choices=["auto", "single", "staged"],
+    p.add_argument("--row-pass", default="auto", choices=["auto", "single", "staged", "push"],
                    help="pin the row pass of the headline workload (default: the library's choice)")
     return p.parse_args()
 
@@ -356,7 +356,7 @@ def main():
     model = W.config_by_name(args.config)
     t0 = time.time()
     ctx = ed.build_local_ops(ed.build_sectors(model), {"auto": ed.OPS_DEFAULT, "single": ed.OPS_ROW_SINGLE,
-                                                       "staged": ed.OPS_ROW_STAGED}[args.row_pass])
+                                                       "staged": ed.OPS_ROW_STAGED, "push": ed.OPS_ROW_PUSH}[args.row_pass])
     t_setup = time.time() - t0
     D = ctx.dim
     tdt = torch.float64 if args.dtype == "f64" else torch.float32

@@ -87,17 +87,20 @@ ed_status ed_build_sectors(const ed_model_desc* model, ed_ctx** out);
  * H_B,s off-diagonals, side diagonals, the cross-cut maps.
  * flags: ED_OPS_DEFAULT, or ED_OPS_FORCE_CSR / ED_OPS_FORCE_DENSE to pin the
  * per-sector choice instead of autotuning it; optionally or-ed with one of
- * ED_OPS_ROW_SINGLE / ED_OPS_ROW_STAGED to pick the row pass of spin models
- * with cross-cut bonds (single, the default: cross terms gathered from x in
- * global memory; staged: each cross term's source row staged in shared
- * memory, one CTA per SM).  The results are identical up to FP summation
- * order (bit-identical in the exact fixed-point FP64 mode).  Synchronises
- * the device. */
+ * one of ED_OPS_ROW_SINGLE / ED_OPS_ROW_STAGED / ED_OPS_ROW_PUSH to pick how
+ * spin models with cross-cut bonds get their cross terms (single, the
+ * default: gathered from x in global memory by the row pass; staged: each
+ * output row stages its source rows in shared memory, one CTA per SM;
+ * push: each source row, staged once, is added into its target rows with
+ * atomic adds).  The results are identical up to FP summation order
+ * (bit-identical in the exact fixed-point FP64 mode; push makes the FP32
+ * summation order run-dependent).  Synchronises the device. */
 #define ED_OPS_DEFAULT 0
 #define ED_OPS_FORCE_CSR 1
 #define ED_OPS_FORCE_DENSE 2
 #define ED_OPS_ROW_SINGLE 4
 #define ED_OPS_ROW_STAGED 8
+#define ED_OPS_ROW_PUSH 16
 ed_status ed_build_local_ops(ed_ctx* ctx, int flags);
 
 /* y = H x over the whole sector (all blocks), device pointers of ed_dim
@@ -269,7 +272,8 @@ ed_status ed_profile_enable(ed_ctx* ctx, int enable);
 ed_status ed_profile_read(ed_ctx* ctx, double* ms, int64_t* count, int reset);
 /* Which row pass ed_apply_H runs for `dtype` on this context: 0 = the
  * plain per-row kernel (the class-sorted kernels do not apply), 1 = the
- * single-row pass (k_row5), 2 = the staged-source row pass (k_rowx);
+ * single-row pass (k_row5), 2 = the staged-source row pass (k_rowx), 3 =
+ * k_row5 without cross terms followed by their scatter-add (k_xpush);
  * negative: ed_build_local_ops has not run. */
 int ed_row_pass(const ed_ctx* ctx, ed_dtype dtype);
 

@@ -15,6 +15,7 @@ from .ed import (  # noqa: E402,F401
     OPS_FORCE_DENSE,
     OPS_ROW_SINGLE,
     OPS_ROW_STAGED,
+    OPS_ROW_PUSH,
     Batch,
     batch_apply,
     batch_create,
@@ -34,4 +35,4 @@ from ._lib import EDError  # noqa: E402,F401
 
 __all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "LanczosResult", "Server", "apply_H", "apply_H_noalloc", "build_local_ops", "build_sectors", "lanczos_gf",
            "lanczos_ground", "random_vector", "EDError", "OPS_DEFAULT", "OPS_FORCE_CSR", "OPS_FORCE_DENSE",
-           "OPS_ROW_SINGLE", "OPS_ROW_STAGED"]
+           "OPS_ROW_SINGLE", "OPS_ROW_STAGED", "OPS_ROW_PUSH"]

@@ -18,6 +18,7 @@ struct P3 {
   int nblk;
   int ncross;
   long long n_rows;
+  int keep_fixed;  // row pass leaves every row as a 64-bit partial sum (cross terms added later)
 };
 
 struct PF32 {

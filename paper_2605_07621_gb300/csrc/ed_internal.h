@@ -211,6 +211,8 @@ struct ed_ctx {
   int4* d_panel_items = nullptr;     // (block, first column, first row, rows) of the H_A pass
   long long* d_grp2_start = nullptr; // per block: first two-row group (plus total)
   long long n_grp2 = 0;
+  long long* d_grp4_start = nullptr; // per block: first four-row group (plus total)
+  long long n_grp4 = 0;
   long long n_panel_items = 0;
   int* d_err = nullptr;              // set by kernels whose bounded waits ran out
   int2* d_rowx = nullptr;            // (block, row) work list of the staged-source row pass

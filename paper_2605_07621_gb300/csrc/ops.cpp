@@ -328,7 +328,8 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
 
 extern "C" ed_status ed_build_local_ops(ed_ctx* c, int flags) {
   if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }
-  if (flags < 0 || flags > 15 || (flags & 3) == 3 || (flags & 12) == 12) {
+  const int rowf = flags & (ED_OPS_ROW_SINGLE | ED_OPS_ROW_STAGED | ED_OPS_ROW_PUSH);
+  if (flags < 0 || flags > 31 || (flags & 3) == 3 || (rowf & (rowf - 1)) != 0) {
     set_error("bad flags %d", flags);
     return ED_EINVAL;
   }
@@ -407,6 +408,15 @@ extern "C" ed_status ed_build_local_ops(ed_ctx* c, int flags) {
     g2.push_back(acc);
     c->n_grp2 = acc;
     ED_TRY(upload(c, &c->d_grp2_start, g2));
+    std::vector<long long> g4;
+    acc = 0;
+    for (const Block& b : c->blocks) {
+      g4.push_back(acc);
+      acc += (b.dA + 3) / 4;
+    }
+    g4.push_back(acc);
+    c->n_grp4 = acc;
+    ED_TRY(upload(c, &c->d_grp4_start, g4));
   }
   c->h_cross.clear();
   for (const auto& cb : c->cross) c->h_cross.push_back(DevCross{cb.ia, cb.ib, cb.coef});

@@ -21,6 +21,7 @@ OPS_FORCE_CSR = 1
 OPS_FORCE_DENSE = 2
 OPS_ROW_SINGLE = 4
 OPS_ROW_STAGED = 8
+OPS_ROW_PUSH = 16
 
 
 def _stream_handle(stream):
@@ -103,7 +104,7 @@ class Context:
 
         dt = L.ED_F32 if dtype in (torch.float32, "f32") else L.ED_F64
         k = int(L.load().ed_row_pass(self._h, dt))
-        return {0: "k_apply_rows", 1: "k_row5", 2: "k_rowx"}.get(k, "none")
+        return {0: "k_apply_rows", 1: "k_row5", 2: "k_rowx", 3: "k_row5+k_xpush"}.get(k, "none")
 
     def profile_read(self, reset: bool = True):
         """(ms per stage [exp_max, to_fixed, row pass, panel pass], number of applies)."""

