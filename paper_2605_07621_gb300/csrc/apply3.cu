@@ -526,18 +526,18 @@ static P3 make_p3(const ed_ctx* c) {
   return p;
 }
 
-// Row-pass shapes: 4-byte types take two rows per pass with 512-thread
-// CTAs, two CTAs per SM (one CTA's TMA copy overlaps the other's compute).
-// 8-byte types take two rows per pass in one 1024-thread CTA per SM (the
-// two staged rows fill the shared memory; the B-side index and map loads
-// are shared by both rows): on the J1-J2 4x8 workload 35.3 ms against
-// 40.9 ms for one row per pass in two 512-thread CTAs (kRow8Pair = false).
+// Row-pass shapes: one 1024-thread CTA per SM whose staged rows fill the
+// shared memory and share the B-side index and map loads: four rows per
+// pass for 4-byte types, two for 8-byte types.  On the J1-J2 4x8 workload
+// this measured 15.7 ms (FP32) and 35.3 ms (FP64) against 23.3 and 40.9 ms
+// for two (FP32) or one (FP64) row per pass in two 512-thread CTAs per SM
+// (kRow4Quad / kRow8Pair = false).
 #ifndef ROW8_PAIR
 #define ROW8_PAIR 1
 #endif
 constexpr bool kRow8Pair = ROW8_PAIR != 0;
 #ifndef ROW4_QUAD
-#define ROW4_QUAD 0
+#define ROW4_QUAD 1
 #endif
 constexpr bool kRow4Quad = ROW4_QUAD != 0;
 static int rows_per_pass(size_t es) { return es == 4 ? (kRow4Quad ? 4 : 2) : (kRow8Pair ? 2 : 1); }
