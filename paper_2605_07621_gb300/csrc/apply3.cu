@@ -171,6 +171,10 @@ __global__ void __launch_bounds__(NT, MINB)
         acc[r] = (da[r] + dbv + Pol::vab(t, z)) * xs[r][b];
       }
       const uint2* cp = t.B_col4 + m.x;
+      // index groups in flight per class step (measured best: 4 for 8-byte
+      // types, 2 for 4-byte types, whose four rows per pass need registers)
+      constexpr int HBU = sizeof(S) == 8 ? 4 : 2;
+      const unsigned zz = (unsigned)dB | ((unsigned)dB << 16);  // four zero-slot indices
 #pragma unroll
       for (int c = 0; c < kMaxCls; ++c) {
         const unsigned n4 = (m.y >> (8 * c)) & 255u;
@@ -178,11 +182,18 @@ __global__ void __launch_bounds__(NT, MINB)
         S sum[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) sum[r] = 0;
-        for (unsigned i = 0; i < n4; ++i) {
-          const uint2 q = __ldg(cp + i);
-          const unsigned i0 = q.x & 0xFFFFu, i1 = q.x >> 16, i2 = q.y & 0xFFFFu, i3 = q.y >> 16;
+        // HBU index groups are loaded before any is used, so their L2
+        // latencies overlap; groups past the class end read the zero slot
+        for (unsigned i = 0; i < n4; i += HBU) {
+          uint2 q[HBU];
 #pragma unroll
-          for (int r = 0; r < R; ++r) sum[r] += (xs[r][i0] + xs[r][i1]) + (xs[r][i2] + xs[r][i3]);
+          for (int u = 0; u < HBU; ++u) q[u] = i + u < n4 ? __ldg(cp + i + u) : make_uint2(zz, zz);
+#pragma unroll
+          for (int u = 0; u < HBU; ++u) {
+            const unsigned i0 = q[u].x & 0xFFFFu, i1 = q[u].x >> 16, i2 = q[u].y & 0xFFFFu, i3 = q[u].y >> 16;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sum[r] += (xs[r][i0] + xs[r][i1]) + (xs[r][i2] + xs[r][i3]);
+          }
         }
         cp += n4;
         const S wc = Pol::w(t, c);
@@ -193,10 +204,10 @@ __global__ void __launch_bounds__(NT, MINB)
         unsigned dr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) dr[r] = r < nr ? (pa[r] ^ pb) : 0u;
-        if constexpr (Pol::kUniformCross) {
-          // floating point: loop over every bond with warp-uniform table
-          // indices (B site, bond, weight); only the validity predicate and
-          // the gather address vary across lanes; one FMA per valid bond
+        if constexpr (sizeof(S) == 4) {
+          // 4-byte types (four rows per pass): loop over every bond with
+          // warp-uniform table indices (B site, bond, weight); only the
+          // validity predicate and the gather address vary across lanes
           for (int ib = 0; ib < t.n_ib; ++ib) {
             const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
             unsigned km = t.ib_mask[ib];
@@ -213,23 +224,48 @@ __global__ void __launch_bounds__(NT, MINB)
             }
           }
         } else {
-          // 64-bit integers: visit only each lane's valid bonds, so the
-          // multiply-adds are not spent on bonds that contribute nothing
+          // 8-byte types (two rows per pass), B cross site by B cross site:
+          // the gathers of the site's first kXB bonds (warp-uniform bond
+          // indices) for both rows are issued before any is summed, so their
+          // latencies overlap; the next site's map entry is loaded one site
+          // ahead.  Bonds beyond kXB at one site take a plain loop.
+          constexpr int kXB = 4;
+          unsigned mq_next = t.n_ib > 0 ? __ldg(t.mapB + gB) : 0u;
           for (int ib = 0; ib < t.n_ib; ++ib) {
-            const unsigned rm = t.ib_mask[ib];
-            unsigned any = 0;
+            const unsigned mq = mq_next;
+            if (ib + 1 < t.n_ib) mq_next = __ldg(t.mapB + (long long)(ib + 1) * t.B_total + gB);
+            unsigned rm = t.ib_mask[ib];
+            int kq[kXB];
 #pragma unroll
-            for (int r = 0; r < R; ++r) any |= dr[r] & rm;
-            if (!any) continue;
-            const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
+            for (int q = 0; q < kXB; ++q) {
+              kq[q] = rm ? __ffs(rm) - 1 : -1;
+              rm &= rm - 1;
+            }
+            S v[R][kXB];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-              unsigned dd = dr[r] & rm;
-              while (dd) {
-                const int k = __ffs(dd) - 1;
-                dd &= dd - 1;
+            for (int q = 0; q < kXB; ++q)
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                v[r][q] = 0;
+                if (kq[q] >= 0 && ((dr[r] >> kq[q]) & 1u)) {
+                  const S* sp = src_row[r][t.bond_ia[kq[q]]];
+                  if (sp) v[r][q] = __ldg(sp + mq);
+                }
+              }
+#pragma unroll
+            for (int q = 0; q < kXB; ++q)
+              if (kq[q] >= 0) {
+                const S w = Pol::bw(t, kq[q]);
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += w * v[r][q];
+              }
+            while (rm) {
+              const int k = __ffs(rm) - 1;
+              rm &= rm - 1;
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
                 const S* sp = src_row[r][t.bond_ia[k]];
-                if (sp) acc[r] += Pol::bw(t, k) * __ldg(sp + mq);
+                if (((dr[r] >> k) & 1u) && sp) acc[r] += Pol::bw(t, k) * __ldg(sp + mq);
               }
             }
           }

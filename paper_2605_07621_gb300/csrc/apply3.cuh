@@ -23,7 +23,6 @@ struct P3 {
 
 struct PF32 {
   using S = float;
-  static constexpr bool kUniformCross = true;
   __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
   __device__ static float bw(const Dev3& t, int k) { return t.bond_w32[k]; }
   __device__ static float diagA(const Dev3& t, long long gA) { return t.A_d32[gA] + t.dc0_32; }
@@ -41,7 +40,6 @@ struct PF32 {
 };
 struct PF64 {
   using S = double;
-  static constexpr bool kUniformCross = true;
   __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
   __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
   __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
@@ -59,7 +57,6 @@ struct PF64 {
 };
 struct PI64 {
   using S = long long;
-  static constexpr bool kUniformCross = false;
   __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
   __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
   __device__ static long long diagA(const Dev3& t, long long gA) { return (long long)t.A_dI[gA] + t.dc0_I; }
