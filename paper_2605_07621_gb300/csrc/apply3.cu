@@ -44,6 +44,11 @@ __global__ void k_to_fixed(const double* __restrict__ x, long long* __restrict__
 }
 
 constexpr int kRowThreads = 512;
+// valid-bond lists for the cross terms also for 4-byte types (kept off: the
+// four-row FP32 pass measured no faster with them)
+#ifndef XL_F32
+#define XL_F32 0
+#endif
 
 // Row pass: work unit = R consecutive rows of one block ("row group").  The
 // rows are brought into shared memory by bulk TMA copies (two CTAs per SM,
@@ -63,6 +68,15 @@ __global__ void __launch_bounds__(NT, MINB)
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem5);
   S* bufs = reinterpret_cast<S*>(smem5 + 128);
   __shared__ const S* src_row[R][32];  // per row, per A cross site
+  // per row, B cross site and value beta of the column's bit at that site:
+  // the site's bonds that are valid there (their A bit differs from beta),
+  // as (source row, weight) lists of at most kXL entries
+  constexpr int kXL = 4;
+  __shared__ const S* xl_ptr[R][32][2][kXL];
+  __shared__ S xl_w[R][32][2][kXL];
+  __shared__ unsigned char xl_n[R][32][2];
+  __shared__ int xl_mx[32];  // per B cross site: longest list over rows and beta
+  constexpr bool kLists = sizeof(S) == 8 || XL_F32;
   __shared__ int s_pad[R];
   constexpr int V = 16 / (int)sizeof(S);
   const Dev3& t = p.t;
@@ -139,6 +153,31 @@ __global__ void __launch_bounds__(NT, MINB)
       }
       src_row[r][ia] = sp;
     }
+    if (kLists && p.ncross && t.xl_ok) {
+      __syncthreads();  // src_row complete
+      if (threadIdx.x < 32) xl_mx[threadIdx.x] = 0;
+      __syncthreads();
+      if (threadIdx.x < R * 64) {
+        const int r = threadIdx.x >> 6, ib = (threadIdx.x >> 1) & 31, beta = threadIdx.x & 1;
+        int n = 0;
+        if (ib < t.n_ib && r < nr) {
+          const unsigned par = t.A_pack[bl.gA0 + a0 + r];
+          unsigned km = t.ib_mask[ib];
+          while (km) {
+            const int k = __ffs(km) - 1;
+            km &= km - 1;
+            const S* sp = src_row[r][t.bond_ia[k]];
+            if ((((par >> k) & 1u) != (unsigned)beta) && sp) {  // at most kXL (xl_ok)
+              xl_ptr[r][ib][beta][n] = sp;
+              xl_w[r][ib][beta][n] = Pol::bw(t, k);
+              ++n;
+            }
+          }
+        }
+        xl_n[r][ib][beta] = (unsigned char)n;
+        atomicMax(&xl_mx[ib], n);
+      }
+    }
     const bool ok = bar_wait(&bar[0], phase);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(err, 1);
@@ -204,7 +243,36 @@ __global__ void __launch_bounds__(NT, MINB)
         unsigned dr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) dr[r] = r < nr ? (pa[r] ^ pb) : 0u;
-        if constexpr (sizeof(S) == 4) {
+        if (kLists && t.xl_ok) {
+          // per B cross site, the column's bit there picks each row's list of
+          // valid bonds; the gathers of all rows' lists are issued before any
+          // is summed, and the next site's map entry is loaded one site ahead
+          unsigned mq_next = t.n_ib > 0 ? __ldg(t.mapB + gB) : 0u;
+          for (int ib = 0; ib < t.n_ib; ++ib) {
+            const unsigned mq = mq_next;
+            if (ib + 1 < t.n_ib) mq_next = __ldg(t.mapB + (long long)(ib + 1) * t.B_total + gB);
+            const int mx = xl_mx[ib];
+            if (!mx) continue;
+            const int beta = (int)((pb >> (__ffs(t.ib_mask[ib]) - 1)) & 1u);
+            int nn[R];
+            S v[R][kXL];
+#pragma unroll
+            for (int r = 0; r < R; ++r) nn[r] = xl_n[r][ib][beta];
+#pragma unroll
+            for (int i = 0; i < kXL; ++i)
+              if (i < mx) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r][i] = i < nn[r] ? __ldg(xl_ptr[r][ib][beta][i] + mq) : (S)0;
+              }
+#pragma unroll
+            for (int i = 0; i < kXL; ++i)
+              if (i < mx) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                  if (i < nn[r]) acc[r] += xl_w[r][ib][beta][i] * v[r][i];
+              }
+          }
+        } else if constexpr (sizeof(S) == 4) {
           // 4-byte types (four rows per pass): loop over every bond with
           // warp-uniform table indices (B site, bond, weight); only the
           // validity predicate and the gather address vary across lanes
@@ -224,11 +292,10 @@ __global__ void __launch_bounds__(NT, MINB)
             }
           }
         } else {
-          // 8-byte types (two rows per pass), B cross site by B cross site:
-          // the gathers of the site's first kXB bonds (warp-uniform bond
-          // indices) for both rows are issued before any is summed, so their
-          // latencies overlap; the next site's map entry is loaded one site
-          // ahead.  Bonds beyond kXB at one site take a plain loop.
+          // 8-byte types with more than kXL bonds at some B cross site: the
+          // gathers of a site's first kXB bonds (warp-uniform bond indices)
+          // for both rows are issued before any is summed; bonds beyond kXB
+          // take a plain loop
           constexpr int kXB = 4;
           unsigned mq_next = t.n_ib > 0 ? __ldg(t.mapB + gB) : 0u;
           for (int ib = 0; ib < t.n_ib; ++ib) {

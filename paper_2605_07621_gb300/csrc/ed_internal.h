@@ -154,6 +154,7 @@ struct Dev3 {
   // cross bonds grouped by B site: bonds with B site ib are bits ib_mask[ib]
   int n_ib;
   int n_ia;
+  int xl_ok;                // every B cross site has at most 4 bonds (row-pass bond lists)
   unsigned ib_mask[32];
   unsigned ia_mask[32];     // bonds (bits) whose A site is ia
   unsigned char bond_ib[32];

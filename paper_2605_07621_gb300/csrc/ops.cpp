@@ -211,6 +211,9 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   }
   t.n_ib = (int)c->crossB_bits.size();
   t.n_ia = (int)c->crossA_bits.size();
+  t.xl_ok = 1;
+  for (int ib = 0; ib < t.n_ib; ++ib)
+    if (__builtin_popcount(t.ib_mask[ib]) > 4) t.xl_ok = 0;
   const DevDiagParams& dp = c->diag;
   t.vab_and = dp.vab_and;
   t.ncls_d = dp.ncls;
