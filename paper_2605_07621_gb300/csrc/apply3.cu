@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(NT, MINB)
           // 4-byte types (four rows per pass): loop over every bond with
           // warp-uniform table indices (B site, bond, weight); only the
           // validity predicate and the gather address vary across lanes
+          unsigned mq_next = t.n_ib > 0 ? __ldg(t.mapB + gB) : 0u;  // map entries one site ahead
           for (int ib = 0; ib < t.n_ib; ++ib) {
-            const unsigned mq = __ldg(t.mapB + (long long)ib * t.B_total + gB);
+            const unsigned mq = mq_next;
+            if (ib + 1 < t.n_ib) mq_next = __ldg(t.mapB + (long long)(ib + 1) * t.B_total + gB);
             unsigned km = t.ib_mask[ib];
             while (km) {
               const int k = __ffs(km) - 1;
