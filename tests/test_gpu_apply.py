@@ -175,7 +175,17 @@ def _dyadic_spin(m):
 CROSS_MODELS = ["heis16", "j1j2_4x4", "j1j2_4x4_strip", "xxz_odd_cut", "xxz_n_up_1"]
 
 
-@pytest.mark.parametrize("name", CROSS_MODELS + ["j1j2_4x6_ragged"])
+EXTRA_CROSS = {
+    # 52 cross bonds: more than the class-sorted kernels take (general kernel)
+    "j1j2_4x6_ragged": lambda: W.j1j2_torus(4, 6, cut_mask=0b101101001011010010110100),
+    # 32 cross bonds, five on one B site: the row pass's general cross loop
+    "j1j2_4x4_crowded": lambda: W.j1j2_torus(4, 4, cut_mask=25011),
+    # 30 cross bonds, six on one B site, 3x6 torus
+    "j1j2_3x6_crowded": lambda: W.j1j2_torus(3, 6, cut_mask=125720),
+}
+
+
+@pytest.mark.parametrize("name", CROSS_MODELS + list(EXTRA_CROSS))
 def test_row_pass_variants(ed, oracle_mod, name):
     """The three ways of adding the cross terms (gathered from global
     memory, gathered from source rows staged in shared memory, pushed from
@@ -184,7 +194,7 @@ def test_row_pass_variants(ed, oracle_mod, name):
     summation-order rounding."""
     import torch
 
-    m = MODELS[name] if name in MODELS else W.j1j2_torus(4, 6, cut_mask=0b101101001011010010110100)
+    m = MODELS[name] if name in MODELS else EXTRA_CROSS[name]()
     okeys = oracle_mod.sector_keys(m)
     ys = {}
     for flags in (ed.OPS_ROW_SINGLE, ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
