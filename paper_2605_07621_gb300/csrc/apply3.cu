@@ -408,6 +408,9 @@ __global__ void __launch_bounds__(256) k_panel3(P3 p, const int4* __restrict__ i
 // first (warp-uniform), then all U x NC neighbour values are loaded before
 // any is summed, so U x NC independent loads per lane overlap their
 // latency instead of one neighbour row at a time.
+// 32 x NC zeros read by k_panel4 in place of missing neighbour rows
+static __device__ __align__(16) long long g_zero_row[256];
+
 template <class Pol, int NC, int U>
 __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ items, long long n_items,
                                                 const typename Pol::S* __restrict__ x, typename Pol::S* __restrict__ y,
@@ -431,6 +434,9 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
     for (int sp = 0; sp < 256; sp += W) {
       const long long b0 = it.y + sp + lane;
       if (it.y + sp >= dB) break;
+      const bool full = it.y + sp + W <= dB;
+      const S* xb0 = xb + b0;                                              // column b0 of row 0
+      const S* zr = reinterpret_cast<const S*>(g_zero_row) + lane;         // zeros at +32c
       S acc[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -445,6 +451,25 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
         S sum[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) sum[c] = 0;
+        if (full) {
+          // full sub-panel: no per-column checks; entries past the class end
+          // read a zero row
+          for (int i0 = 0; i0 < n; i0 += U) {
+            const S* rp[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              rp[u] = i0 + u < n ? xb0 + (long long)t.A_col[e + i0 + u] * dB : zr;
+            S v[U][NC];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int c = 0; c < NC; ++c) v[u][c] = __ldg(rp[u] + 32 * c);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int c = 0; c < NC; ++c) sum[c] += v[u][c];
+          }
+        } else {
         for (int i0 = 0; i0 < n; i0 += U) {
           long long rowoff[U];
 #pragma unroll
@@ -461,6 +486,7 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
           for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < NC; ++c) sum[c] += v[u][c];
+        }
         }
         e += n;
         const S wc = Pol::w(t, cl);
@@ -765,13 +791,13 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
   if (c->n_panel_items > 0) {
     const long long g2 = std::min<long long>(c->n_panel_items, (long long)sms * 8);
     // measured on the 4x8 J1-J2 and 4x4 Hubbard workloads: 8-byte types
-    // gain from two neighbour rows in flight on 128-column sub-panels
-    // (24.5 -> 13.3 ms, 5.1 -> 2.5 ms), FP32 is fastest one row at a time on
-    // full 256-column panels
+    // gain from four neighbour rows in flight on 128-column sub-panels
+    // (one row at a time: 24.5 / 5.1 ms; four: 9.9 / 2.0 ms), FP32 is fastest
+    // one row at a time on full 256-column panels
     if constexpr (sizeof(typename Pol::S) == 4)
       k_panel3<Pol><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
     else
-      k_panel4<Pol, 4, 2><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
+      k_panel4<Pol, 4, 4><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
     ED_CUDA_TRY(cudaGetLastError());
   }
   if constexpr (sizeof(typename Pol::S) == 8 && !std::is_floating_point<typename Pol::S>::value) {
