@@ -9,9 +9,10 @@
 //         tens of T/s, so no FP64 instruction is issued per matrix element.
 // Row pass: psi_s[a,:] is staged in shared memory by bulk TMA copies, then
 // each column b sums, class by class, the H_B neighbours (16-bit column
-// indices) and the cross-cut gathers, plus the diagonal.  Two row passes:
-// k_row5 (here) gathers the cross terms from x in global memory; k_rowx
-// (rowx.cuh) also stages each cross term's source row in shared memory.
+// indices) and the cross-cut gathers, plus the diagonal.  Three forms of the
+// cross terms: k_row5 (here, default) gathers them from x in global memory;
+// k_rowx (rowx.cuh) stages each cross term's source row in shared memory;
+// k_xpush (here) pushes them from staged source rows with atomic adds.
 // Panel pass: the H_A (row-mixing) term over column panels that stay
 // resident in L2.
 #include <mutex>
@@ -50,14 +51,17 @@ constexpr int kRowThreads = 512;
 #define XL_F32 0
 #endif
 
-// Row pass: work unit = R consecutive rows of one block ("row group").  The
-// rows are brought into shared memory by bulk TMA copies (two CTAs per SM,
-// so one CTA's copy overlaps the other's compute).  Per column b:
+// Row pass: work unit = R consecutive rows of one block ("row group"),
+// brought into shared memory by bulk TMA copies; one 1024-thread CTA per SM
+// whose R staged rows (4 for 4-byte, 2 for 8-byte types) share every B-side
+// load.  Per column b:
 //  * H_B: the class segments of the column's index list are padded to
-//    groups of four 16-bit indices, read with one 8-byte load per group and
-//    gathered from all R staged rows (padding points at a zero slot);
+//    groups of four 16-bit indices, read with one 8-byte load per group
+//    (several groups loaded ahead) and gathered from all R staged rows
+//    (padding points at a zero slot);
 //  * cross terms: one B-side map load per B cross site, shared by the R
-//    rows, then one gather per valid bond from the neighbouring block;
+//    rows, then one gather per valid bond from the neighbouring block (8-byte
+//    types: from per-row lists of the valid bonds for each column bit);
 //  * the diagonal from per-row constants and popcounts of packed words.
 template <class Pol, int R, int NT = kRowThreads, int MINB = 2>
 __global__ void __launch_bounds__(NT, MINB)
