@@ -435,7 +435,7 @@ def main():
         traffic = None
     # dominant kernel: the row pass (stage 2) -- reads every row of x once and
     # writes every element of y once, i.e. the algorithmic bytes of H|psi>
-    names = ["k_exp_max", "k_to_fixed", ctx.row_pass(tdt), "k_panel3" if tdt == torch.float32 else "k_panel4"]
+    names = ["k_exp_max", "k_to_fixed", ctx.row_pass(tdt), "k_panel4"]
     dom = int(np.argmax(stage_ms))
     dom_ms = float(stage_ms[dom])
     achieved_dom = alg_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None

@@ -352,69 +352,17 @@ __global__ void __launch_bounds__(NT, MINB)
   }
 }
 
-template <class Pol>
-__global__ void __launch_bounds__(256) k_panel3(P3 p, const int4* __restrict__ items, long long n_items,
-                                                const typename Pol::S* __restrict__ x, typename Pol::S* __restrict__ y,
-                                                const int* __restrict__ emax) {
-  using S = typename Pol::S;
-  constexpr int NC = 8;  // columns per lane: panels of 256 columns
-  const Dev3& t = p.t;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e2 = emax ? out_exp(t, emax) : 0;
-  for (long long w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int4 it = items[w];
-    if (warp >= it.w) continue;
-    const DevBlock bl = p.blocks[it.x];
-    const long long a = it.z + warp;
-    const long long gA = bl.gA0 + a;
-    const long long dB = bl.dB;
-    const S* xb = x + bl.off;
-    S* yrow = y + bl.off + a * dB;
-    S acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const long long b = it.y + lane + 32 * c;
-      acc[c] = b < dB ? yrow[b] : (S)0;
-    }
-    const uint2 m = t.A_meta[gA];
-    unsigned e = m.x;
-#pragma unroll
-    for (int cl = 0; cl < kMaxCls; ++cl) {
-      const unsigned n = (m.y >> (8 * cl)) & 255u;
-      if (!n) continue;
-      S sum[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) sum[c] = 0;
-      for (unsigned i = 0; i < n; ++i) {
-        const S* xr = xb + (long long)t.A_col[e + i] * dB;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const long long b = it.y + lane + 32 * c;
-          if (b < dB) sum[c] += __ldg(xr + b);
-        }
-      }
-      e += n;
-      const S wc = Pol::w(t, cl);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += wc * sum[c];
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const long long b = it.y + lane + 32 * c;
-      if (b < dB) store_out<Pol>(yrow, b, acc[c], true, e2);
-    }
-  }
-}
+// 32 x NC zeros read by k_panel4 in place of missing neighbour rows
+static __device__ __align__(16) long long g_zero_row[256];
 
 // H_A panel pass with U neighbour rows in flight per class step: each warp
 // owns one output row of a 256-column panel, processed as sub-panels of
 // 32 * NC columns; the column indices of U consecutive H_A entries are read
 // first (warp-uniform), then all U x NC neighbour values are loaded before
 // any is summed, so U x NC independent loads per lane overlap their
-// latency instead of one neighbour row at a time.
-// 32 x NC zeros read by k_panel4 in place of missing neighbour rows
-static __device__ __align__(16) long long g_zero_row[256];
-
+// latency instead of one neighbour row at a time.  Full sub-panels need no
+// per-column checks, and entries past a class's end read the zero row, so
+// their loads carry no predicates.
 template <class Pol, int NC, int U>
 __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ items, long long n_items,
                                                 const typename Pol::S* __restrict__ x, typename Pol::S* __restrict__ y,
@@ -796,10 +744,10 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
     const long long g2 = std::min<long long>(c->n_panel_items, (long long)sms * 8);
     // measured on the 4x8 J1-J2 and 4x4 Hubbard workloads: 8-byte types
     // gain from four neighbour rows in flight on 128-column sub-panels
-    // (one row at a time: 24.5 / 5.1 ms; four: 9.9 / 2.0 ms), FP32 is fastest
-    // one row at a time on full 256-column panels
+    // (one row at a time: 24.5 / 5.1 ms; four: 9.9 / 2.0 ms), FP32 from two
+    // rows in flight on full 256-column panels (6.2 -> 5.4 ms on J1-J2 4x8)
     if constexpr (sizeof(typename Pol::S) == 4)
-      k_panel3<Pol><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
+      k_panel4<Pol, 8, 2><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
     else
       k_panel4<Pol, 4, 4><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
     ED_CUDA_TRY(cudaGetLastError());
