@@ -110,6 +110,14 @@ struct RunOut {
 // Three-term Lanczos recurrence from the normalised v0 (device, type T).
 // resid_tol > 0 additionally requires the Ritz residual estimate
 // beta_m |s_m| <= resid_tol (used when an eigenvector is wanted).
+//
+// alpha_j, beta_{j+1} stay on the device (a history array) and are read
+// back only every `check_every` steps (every kReadEvery in fixed-length
+// runs), so the host does not synchronise with the GPU at every step.  A
+// breakdown (beta ~ 0) is found at the next read; the steps run after it
+// (on an invalid vector) are discarded, and the run ends at the breakdown.
+constexpr int kReadEvery = 16;
+
 template <typename T>
 ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_iter, double tol, int check_every,
                  bool fixed, bool reorth, Basis* basis, RunOut& out, double resid_tol = 0.0) {
@@ -117,6 +125,10 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   T* vprev = bufs[0];
   T* v = bufs[1];
   T* w = bufs[2];
+  DevBuf mem;
+  double* hist = nullptr;  // [max_iter][2]: alpha_j, beta_{j+1}
+  ED_TRY(mem.get((void**)&hist, (size_t)max_iter * 2 * sizeof(double)));
+  std::vector<double> hbuf;
   ED_CUDA_TRY(cudaMemcpyAsync(v, v0, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
   basis_store<T>(c, basis, v, n, st);
   out.alpha.clear();
@@ -124,7 +136,10 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   out.converged = false;
   double theta_prev = NAN;
   double scale = 0.0;
-  for (int j = 0; j < max_iter; ++j) {
+  const int every = fixed ? kReadEvery : check_every;
+  int read = 0;  // steps whose scalars the host holds
+  bool done = false;
+  for (int j = 0; j < max_iter && !done; ++j) {
     ED_TRY(apply_H_impl(c, v, w, dtype_of<T>(), st));
     launch_lz_a<T>(c, w, v, vprev, j > 0 ? 1 : 0, n, st);
     launch_lz_b<T>(c, w, v, n, st);
@@ -134,38 +149,54 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
         launch_reorth<T>(c, (const T*)basis->base, n, basis->count, w, n, hcoef(c), st);
       ED_TRY(dot_dev<T>(c, w, w, n, slot(c, 1), st, 1));
     }
+    ED_CUDA_TRY(cudaMemcpyAsync(hist + 2 * j, slot(c, 0), 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     ED_CUDA_TRY(cudaGetLastError());
-    double ab[2];
-    ED_TRY(read_scalars(c, 0, 2, ab, st));
-    out.alpha.push_back(ab[0]);
-    out.beta.push_back(ab[1]);
-    scale = std::max(scale, std::fabs(ab[0]) + ab[1]);
     const int m = j + 1;
-    const bool breakdown = ab[1] <= 1e-13 * (scale > 0 ? scale : 1.0);
-    if (!fixed && (m % check_every == 0 || breakdown)) {
-      double th = tridiag_lowest(out.alpha.data(), out.beta.data(), m);
-      bool ok = std::fabs(th - theta_prev) <= tol * std::fabs(th);
-      if (ok && resid_tol > 0.0 && !breakdown) {
-        std::vector<double> sv;
-        tridiag_vector(out.alpha.data(), out.beta.data(), m, th, sv);
-        ok = std::fabs(ab[1] * sv[m - 1]) <= resid_tol * std::max(1.0, std::fabs(th));
+    if (m % every == 0 || m == max_iter) {
+      // read the new steps' scalars and examine them in order
+      hbuf.resize((size_t)(m - read) * 2);
+      ED_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), hist + 2 * read, hbuf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                  st));
+      ED_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int k = read; k < m && !done; ++k) {
+        const double a = hbuf[2 * (k - read)], b = hbuf[2 * (k - read) + 1];
+        out.alpha.push_back(a);
+        out.beta.push_back(b);
+        scale = std::max(scale, std::fabs(a) + b);
+        const int mk = k + 1;
+        const bool breakdown = !(b > 1e-13 * (scale > 0 ? scale : 1.0));
+        if (!fixed && (mk % check_every == 0 || breakdown)) {
+          double th = tridiag_lowest(out.alpha.data(), out.beta.data(), mk);
+          bool ok = std::fabs(th - theta_prev) <= tol * std::fabs(th);
+          if (ok && resid_tol > 0.0 && !breakdown) {
+            std::vector<double> sv;
+            tridiag_vector(out.alpha.data(), out.beta.data(), mk, th, sv);
+            ok = std::fabs(b * sv[mk - 1]) <= resid_tol * std::max(1.0, std::fabs(th));
+          }
+          if (ok) {
+            out.converged = true;
+            done = true;
+          }
+          theta_prev = th;
+        }
+        if (breakdown) {
+          out.converged = true;  // invariant subspace: T is exact
+          done = true;
+        }
       }
-      if (ok) {
-        out.converged = true;
-        break;
-      }
-      theta_prev = th;
-    }
-    if (breakdown) {
-      out.converged = true;  // invariant subspace: T is exact
-      break;
+      read = m;
+      if (done) break;
     }
     if (m == max_iter) break;
     launch_lz_c<T>(c, w, vprev, n, st);
     std::swap(vprev, v);
     basis_store<T>(c, basis, v, n, st);
   }
-  out.theta = tridiag_lowest(out.alpha.data(), out.beta.data(), (int)out.alpha.size());
+  // stop at the step the host examined last (later steps, if any, came
+  // after a breakdown or convergence inside a read batch)
+  const int steps = (int)out.alpha.size();
+  out.theta = tridiag_lowest(out.alpha.data(), out.beta.data(), steps);
+  if (basis && basis->count > steps) basis->count = steps;
   bufs[0] = vprev;
   bufs[1] = v;
   return ED_OK;
