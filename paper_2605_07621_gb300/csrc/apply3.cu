@@ -777,6 +777,23 @@ static ed_status apply_fixed(ed_ctx* c, const double* x, double* y, long long* f
   return run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm);
 }
 
+bool fixed_path(const ed_ctx* c, const void* x) { return c->dyadic && v3_usable(c, ED_F64, x); }
+
+ed_status apply_prepared_fixed(ed_ctx* c, double* y, cudaStream_t st) {
+  if (!c->d_fixed) {
+    set_error("fixed-point input was not prepared");
+    return ED_EINVAL;
+  }
+  ProfMarks pm;
+  pm.begin(c);
+  pm.mark(0, st);
+  pm.mark(1, st);
+  const ed_status r = run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st, pm);
+  pm.mark(4, st);
+  pm.end(c);
+  return r;
+}
+
 ed_status apply_v3(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t st) {
   ProfMarks pm;
   pm.begin(c);

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "krylov.h"
@@ -139,10 +140,30 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   const int every = fixed ? kReadEvery : check_every;
   int read = 0;  // steps whose scalars the host holds
   bool done = false;
+  // FP64 on the exact fixed-point path without reorthogonalisation: lz_c
+  // writes the next step's fixed-point input and its scale, so the apply
+  // skips its own exponent and conversion passes
+  bool fuse = false, prepared = false;
+  if constexpr (std::is_same<T, double>::value) fuse = !reorth && fixed_path(c, v);
+  int* ew = c->d_exp + 1;
   for (int j = 0; j < max_iter && !done; ++j) {
-    ED_TRY(apply_H_impl(c, v, w, dtype_of<T>(), st));
+    if constexpr (std::is_same<T, double>::value) {
+      if (prepared)
+        ED_TRY(apply_prepared_fixed(c, w, st));
+      else
+        ED_TRY(apply_H_impl(c, v, w, dtype_of<T>(), st));
+    } else {
+      ED_TRY(apply_H_impl(c, v, w, dtype_of<T>(), st));
+    }
     launch_lz_a<T>(c, w, v, vprev, j > 0 ? 1 : 0, n, st);
-    launch_lz_b<T>(c, w, v, n, st);
+    if constexpr (std::is_same<T, double>::value) {
+      if (fuse)
+        launch_lz_b_emax(c, w, v, n, ew, st);
+      else
+        launch_lz_b<T>(c, w, v, n, st);
+    } else {
+      launch_lz_b<T>(c, w, v, n, st);
+    }
     if (reorth && basis && basis->kind == BASIS_SAME && basis->complete && basis->count <= kMaxBasis) {
       // classical Gram-Schmidt against all kept vectors, applied twice
       for (int pass = 0; pass < 2; ++pass)
@@ -188,7 +209,16 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
       if (done) break;
     }
     if (m == max_iter) break;
-    launch_lz_c<T>(c, w, vprev, n, st);
+    if constexpr (std::is_same<T, double>::value) {
+      if (fuse && c->d_fixed) {
+        launch_lz_c_fixed(c, w, vprev, c->d_fixed, ew, c->d_exp, n, st);
+        prepared = true;
+      } else {
+        launch_lz_c<T>(c, w, vprev, n, st);
+      }
+    } else {
+      launch_lz_c<T>(c, w, vprev, n, st);
+    }
     std::swap(vprev, v);
     basis_store<T>(c, basis, v, n, st);
   }

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <vector>
 
+#include "apply3.cuh"
 #include "ed_internal.h"
 #include "krylov.h"
 #include "reduce.cuh"
@@ -66,6 +67,44 @@ __global__ void k_lz_b(T* __restrict__ w, const T* __restrict__ v, const double*
   }
   double s = block_sum(acc.value());
   if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// FP64 with the exact fixed-point H|psi>: w -= alpha * v, partial ||w||^2,
+// and the largest biased exponent of w (atomic max into *ew, zeroed before)
+__global__ void k_lz_b_emax(double* __restrict__ w, const double* __restrict__ v, const double* alpha, long long n,
+                            double* part, int* ew) {
+  const double al = alpha[0];
+  DotAcc<double> acc;
+  int em = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wi = w[i] - al * v[i];
+    w[i] = wi;
+    acc.add_prod(wi, wi);
+    em = max(em, (int)(((unsigned long long)__double_as_longlong(wi) >> 52) & 0x7ffull));
+  }
+  for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_down_sync(0xffffffffu, em, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(ew, em);
+  double s = block_sum(acc.value());
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// out = w / beta, and the fixed-point copy X of out that the next H|psi>
+// takes: |out| < 2^E with E = E(max|w|) - E(beta) + 1 (E(y): 2^(E-1) <= |y|
+// < 2^E), X = round(out * 2^(P - E)); the biased-exponent form of E
+// (E + 1022) goes to *ex for the apply's output scale
+__global__ void k_lz_c_fixed(const double* __restrict__ w, double* __restrict__ out, long long* __restrict__ X,
+                             const double* beta, const int* ew, int* ex, int P, long long n) {
+  const double b = beta[0];
+  const double inv = b > 0.0 ? 1.0 / b : 0.0;
+  const int eb = (int)(((unsigned long long)__double_as_longlong(b) >> 52) & 0x7ffull);
+  const int E = (ew[0] - 1022) - (eb - 1022) + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ex[0] = E + 1022;
+  const int sh = P - E;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double o = w[i] * inv;
+    out[i] = o;
+    X[i] = to_fixed(o, sh);
+  }
 }
 
 // out = w / beta
@@ -389,6 +428,16 @@ void launch_lz_b(ed_ctx* c, T* w, const T* v, long long n, cudaStream_t st) {
 template <typename T>
 void launch_lz_c(ed_ctx* c, const T* w, T* out, long long n, cudaStream_t st) {
   k_lz_c<T><<<grid_for(c, n), kRedThreads, 0, st>>>(w, out, slot(c, 1), n);
+}
+void launch_lz_b_emax(ed_ctx* c, double* w, const double* v, long long n, int* ew, cudaStream_t st) {
+  int g = grid_for(c, n);
+  cudaMemsetAsync(ew, 0, sizeof(int), st);
+  k_lz_b_emax<<<g, kRedThreads, 0, st>>>(w, v, slot(c, 0), n, c->d_partials, ew);
+  k_finalize<<<1, kRedThreads, 0, st>>>(c->d_partials, g, slot(c, 1), 1);
+}
+void launch_lz_c_fixed(ed_ctx* c, const double* w, double* out, long long* X, const int* ew, int* ex, long long n,
+                       cudaStream_t st) {
+  k_lz_c_fixed<<<grid_for(c, n), kRedThreads, 0, st>>>(w, out, X, slot(c, 1), ew, ex, c->t3.P, n);
 }
 template <typename T>
 void launch_lz_rerun(ed_ctx* c, const T* w, const T* v, const T* vprev, double alpha, double beta, double inv_next,

@@ -32,6 +32,17 @@ template <typename T>
 void launch_lz_b(ed_ctx* c, T* w, const T* v, long long n, cudaStream_t st);
 template <typename T>
 void launch_lz_c(ed_ctx* c, const T* w, T* out, long long n, cudaStream_t st);
+// FP64 Lanczos steps that hand the next H|psi> its fixed-point input:
+// lz_b also records the largest exponent of w in *ew; lz_c also writes the
+// fixed-point copy X of w / beta and its scale (biased exponent) to *ex
+void launch_lz_b_emax(ed_ctx* c, double* w, const double* v, long long n, int* ew, cudaStream_t st);
+void launch_lz_c_fixed(ed_ctx* c, const double* w, double* out, long long* X, const int* ew, int* ex, long long n,
+                       cudaStream_t st);
+// H|psi> of the exact fixed-point path from an input already converted
+// (c->d_fixed with the scale in c->d_exp[0]); y receives FP64
+ed_status apply_prepared_fixed(ed_ctx* c, double* y, cudaStream_t st);
+// the fixed-point FP64 path applies to x on this context
+bool fixed_path(const ed_ctx* c, const void* x);
 template <typename T>
 void launch_lz_rerun(ed_ctx* c, const T* w, const T* v, const T* vprev, double alpha, double beta, double inv_next,
                      T* out, long long n, cudaStream_t st);
