@@ -45,11 +45,9 @@ __global__ void k_to_fixed(const double* __restrict__ x, long long* __restrict__
 }
 
 constexpr int kRowThreads = 512;
-// valid-bond lists for the cross terms also for 4-byte types (kept off: the
-// four-row FP32 pass measured no faster with them)
-#ifndef XL_F32
-#define XL_F32 0
-#endif
+// valid-bond lists for the cross terms also for 4-byte types (off: the
+// four-row FP32 pass measured slower with them, 17.2 vs 15.5 ms)
+constexpr bool kListsF32 = false;
 
 // Row pass: work unit = R consecutive rows of one block ("row group"),
 // brought into shared memory by bulk TMA copies; one 1024-thread CTA per SM
@@ -80,7 +78,7 @@ __global__ void __launch_bounds__(NT, MINB)
   __shared__ S xl_w[R][32][2][kXL];
   __shared__ unsigned char xl_n[R][32][2];
   __shared__ int xl_mx[32];  // per B cross site: longest list over rows and beta
-  constexpr bool kLists = sizeof(S) == 8 || XL_F32;
+  constexpr bool kLists = sizeof(S) == 8 || kListsF32;
   __shared__ int s_pad[R];
   constexpr int V = 16 / (int)sizeof(S);
   const Dev3& t = p.t;
@@ -615,14 +613,8 @@ static P3 make_p3(const ed_ctx* c) {
 // this measured 15.7 ms (FP32) and 35.3 ms (FP64) against 23.3 and 40.9 ms
 // for two (FP32) or one (FP64) row per pass in two 512-thread CTAs per SM
 // (kRow4Quad / kRow8Pair = false).
-#ifndef ROW8_PAIR
-#define ROW8_PAIR 1
-#endif
-constexpr bool kRow8Pair = ROW8_PAIR != 0;
-#ifndef ROW4_QUAD
-#define ROW4_QUAD 1
-#endif
-constexpr bool kRow4Quad = ROW4_QUAD != 0;
+constexpr bool kRow8Pair = true;
+constexpr bool kRow4Quad = true;
 static int rows_per_pass(size_t es) { return es == 4 ? (kRow4Quad ? 4 : 2) : (kRow8Pair ? 2 : 1); }
 
 static size_t v3_smem(const ed_ctx* c, size_t es, long long* stage_elems) {
