@@ -94,7 +94,7 @@ def sum_over_ranks(value: float, world: int, device: str = "cpu") -> float:
 def kernel_source_hash():
     h = hashlib.sha256()
     for fn in ("apply3.cu", "apply3.cuh", "rowx.cuh", "rowx_f32.cu", "rowx_f64.cu", "rowx_i64.cu", "ed_internal.h",
-               "ops.cpp"):
+               "ops.cpp", "sectors.cpp"):
         with open(os.path.join(ROOT, "paper_2605_07621_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -48,6 +48,10 @@ enum BasisKind { BASIS_NONE = 0, BASIS_SAME = 1, BASIS_BF16 = 2 };
 
 // relative Ritz-residual target when an eigenvector is returned
 constexpr double kVecResid = 1e-10;
+// mixed precision: Ritz residual estimate (relative) at which the FP32 run
+// hands over, and the FP64 refinement's convergence-check interval
+constexpr double kLowResid = 3e-6;
+constexpr int kRefineCheck = 3;
 
 // Lanczos basis kept on the device as one contiguous array of `cap`
 // vectors (same type as the recurrence, or BF16 when only a restart vector
@@ -86,6 +90,12 @@ struct Basis {
     return true;
   }
   void* at(int j) const { return (char*)base + (size_t)j * (size_t)n * elem; }
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    complete = false;
+    count = 0;
+  }
 };
 
 template <typename T>
@@ -240,8 +250,13 @@ ed_status lz_vector(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, const R
   const int m = (int)r.alpha.size();
   std::vector<double> s;
   tridiag_vector(r.alpha.data(), r.beta.data(), m, r.theta, s);
-  ED_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), st));
-  if (basis && basis->complete && basis->count >= m) {
+  const bool combine = std::is_same<T, float>::value && basis && basis->complete && basis->count >= m &&
+                       basis->kind == BASIS_SAME && m <= kMaxBasis;
+  if (!combine) ED_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), st));
+  if (combine) {
+    // one pass over the stored FP32 vectors, float-float sums
+    ED_TRY(launch_combine_f32(c, (const float*)basis->base, n, s.data(), m, x, st));
+  } else if (basis && basis->complete && basis->count >= m) {
     for (int j = 0; j < m; ++j) {
       if (basis->kind == BASIS_BF16)
         launch_axpy_basis<__nv_bfloat16, double>(c, (const __nv_bfloat16*)basis->at(j), x, s[j], n, st);
@@ -386,14 +401,23 @@ extern "C" ed_status ed_lanczos_ground(ed_ctx* c, const ed_lanczos_opts* opts_in
     Basis B;
     if (mixed || want_vec || o.reorth) {
       // keep the basis in FP32 when it fits, else in BF16 (a restart vector
-      // needs only a few digits), else recompute it in a second pass
-      if (!B.init(BASIS_SAME, sizeof(float), n, max_iter + 1, budget) && !o.reorth)
-        B.init(BASIS_BF16, 2, n, max_iter + 1, budget);
+      // needs only a few digits), else recompute it in a second pass.  The
+      // basis may take all free memory but what the steps after this run
+      // allocate (the FP64 vectors of the refinement, or the result and a
+      // residual vector); it is released before the refinement starts
+      const size_t later = (size_t)n * sizeof(double) * (mixed ? 6 : 2) + ((size_t)1 << 30);
+      const size_t fr = free_device_bytes();
+      const size_t budget32 = fr > later ? fr - later : 0;
+      if (!B.init(BASIS_SAME, sizeof(float), n, max_iter + 1, budget32) && !o.reorth)
+        B.init(BASIS_BF16, 2, n, max_iter + 1, budget32);
     }
+    // mixed: the FP32 run goes on until its Ritz vector is close to the
+    // FP32 floor (residual estimate), so that the FP64 refinement starts
+    // from a vector that needs only a few steps
     const double tol_low = mixed ? std::max(o.tol, 2e-7) : o.tol;
     RunOut r;
     ED_TRY(lz_run<float>(c, st, bufs32, v0f, max_iter, tol_low, o.check_every, o.fixed_iter != 0, o.reorth != 0, &B,
-                         r));
+                         r, mixed ? kLowResid : 0.0));
     record_ab(r);
     R.iterations = R.iterations_low = (int)r.alpha.size();
     R.e_low = r.theta;
@@ -402,6 +426,7 @@ extern "C" ed_status ed_lanczos_ground(ed_ctx* c, const ed_lanczos_opts* opts_in
     if (mixed || want_vec) {
       ED_TRY(mem.get((void**)&x, n * sizeof(double)));
       ED_TRY(lz_vector<float>(c, st, bufs32, v0f, r, &B, x));
+      B.release();
     }
     if (mixed) {
       // FP64 refinement: Lanczos restarted from the FP32 Ritz vector until
@@ -412,13 +437,13 @@ extern "C" ed_status ed_lanczos_ground(ed_ctx* c, const ed_lanczos_opts* opts_in
       ED_TRY(mem.get((void**)&xnew, n * sizeof(double)));
       double e_prev = r.theta;
       converged = false;
-      const int blk = std::max(o.refine_block, 2 * o.check_every);
+      const int ce = std::min(o.check_every, kRefineCheck);
+      const int blk = std::max(o.refine_block, 2 * ce);
       for (int rs = 0; rs < 20; ++rs) {
         Basis B64;
         if (want_vec) B64.init(BASIS_SAME, sizeof(double), n, blk + 1, free_device_bytes() / 2);
         RunOut r2;
-        ED_TRY(lz_run<double>(c, st, bufs, x, blk, o.tol, o.check_every, false, false, &B64, r2,
-                              want_vec ? kVecResid : 0.0));
+        ED_TRY(lz_run<double>(c, st, bufs, x, blk, o.tol, ce, false, false, &B64, r2, want_vec ? kVecResid : 0.0));
         R.iterations += (int)r2.alpha.size();
         R.restarts += 1;
         energy = r2.theta;

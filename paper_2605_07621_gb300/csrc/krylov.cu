@@ -164,6 +164,43 @@ __global__ void k_axpy_basis(const TB* __restrict__ v, TO* __restrict__ x, doubl
     x[i] = from_d<TO>(to_d(x[i]) + s * to_d(v[i]));
 }
 
+// x = sum_j s_j V_j over an FP32 basis (V_j = V + j n).  Each coefficient
+// comes as a float pair (hi, lo), s_j = hi + lo to about 48 bits; the
+// product hi * v is split exactly by an fma into its rounded value and
+// error, and the terms are summed in float-float arithmetic (Knuth's
+// TwoSum), so the combination carries about 42 bits without one FP64
+// instruction per term.  The explicit _rn operations keep the compiler
+// from contracting the error-free transformations.
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float2 c, float v) {
+  const float p = __fmul_rn(c.x, v);
+  const float pe = fmaf(c.y, v, fmaf(c.x, v, -p));
+  const float t = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(t, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  hi = t;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+__global__ void k_combine_f32(const float* __restrict__ V, long long n, int m, const float2* __restrict__ s,
+                              double* __restrict__ x) {
+  extern __shared__ float2 sc[];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) sc[j] = s[j];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float hi = 0.f, lo = 0.f;
+    int j = 0;
+    for (; j + 4 <= m; j += 4) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(V + (long long)(j + u) * n + i);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ff_acc(hi, lo, sc[j + u], v[u]);
+    }
+    for (; j < m; ++j) ff_acc(hi, lo, sc[j], __ldg(V + (long long)j * n + i));
+    x[i] = (double)hi + (double)lo;
+  }
+}
+
 // Continued fraction G(w) = CF_p(w + i eta + E0) - CF_h(E0 - w - i eta),
 // CF(z) = w0 / (z - a0 - b1^2 / (z - a1 - ...)), one thread per frequency.
 __device__ __forceinline__ void cf_eval(double zr, double zi, const double* a, const double* b, int m, double w0,
@@ -451,6 +488,25 @@ void launch_scale_cvt(ed_ctx* c, const TI* x, TO* y, double s, long long n, cuda
 template <typename TB, typename TO>
 void launch_axpy_basis(ed_ctx* c, const TB* v, TO* x, double s, long long n, cudaStream_t st) {
   k_axpy_basis<TB, TO><<<grid_for(c, n), kRedThreads, 0, st>>>(v, x, s, n);
+}
+ed_status launch_combine_f32(ed_ctx* c, const float* V, long long n, const double* s, int m, double* x,
+                             cudaStream_t st) {
+  if (m < 1 || m > kMaxBasis) {
+    set_error("basis combination of %d vectors outside 1..%d", m, kMaxBasis);
+    return ED_EINVAL;
+  }
+  std::vector<float2> h(m);
+  for (int j = 0; j < m; ++j) {
+    h[j].x = (float)s[j];
+    h[j].y = (float)(s[j] - (double)h[j].x);
+  }
+  // the pairs travel through the reorthogonalisation coefficient buffer
+  // (kMaxBasis 8-byte slots)
+  float2* d = reinterpret_cast<float2*>(hcoef(c));
+  ED_CUDA_TRY(cudaMemcpyAsync(d, h.data(), (size_t)m * sizeof(float2), cudaMemcpyHostToDevice, st));
+  k_combine_f32<<<grid_for(c, n), kRedThreads, (size_t)m * sizeof(float2), st>>>(V, n, m, d, x);
+  ED_CUDA_TRY(cudaGetLastError());
+  return ED_OK;
 }
 template <typename TI, typename TO>
 void launch_cvt(ed_ctx* c, const TI* x, TO* y, long long n, cudaStream_t st) {

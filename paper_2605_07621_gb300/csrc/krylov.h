@@ -52,6 +52,9 @@ template <typename TB, typename TO>
 void launch_axpy_basis(ed_ctx* c, const TB* v, TO* x, double s, long long n, cudaStream_t st);
 template <typename TI, typename TO>
 void launch_cvt(ed_ctx* c, const TI* x, TO* y, long long n, cudaStream_t st);
+// x = sum_j s_j V_j over m <= kMaxBasis FP32 vectors V_j = V + j n (float-float sums)
+ed_status launch_combine_f32(ed_ctx* c, const float* V, long long n, const double* s, int m, double* x,
+                             cudaStream_t st);
 template <typename T>
 void launch_axpy_dev(ed_ctx* c, const T* x, T* y, const double* s, double sign, long long n, cudaStream_t st);
 template <typename T>

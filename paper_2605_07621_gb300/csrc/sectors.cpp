@@ -154,10 +154,25 @@ extern "C" ed_status ed_build_sectors(const ed_model_desc* m, ed_ctx** out) {
   std::vector<int> sitesA, sitesB, local(n, -1);
   std::vector<char> sideOf(n, 0);  // 0 = A, 1 = B
   if (c->kind == ED_SPIN) {
-    for (int i = 0; i < n; ++i) {
-      if ((m->cut_mask >> i) & 1ULL) { local[i] = (int)sitesA.size(); sitesA.push_back(i); sideOf[i] = 0; }
-      else { local[i] = (int)sitesB.size(); sitesB.push_back(i); sideOf[i] = 1; }
+    // side-local bit order.  On side B the sites on a cross-cut bond take the
+    // high bits: the columns with one configuration of those sites are then a
+    // contiguous run, and flipping one of them maps the run onto a run of the
+    // neighbouring block shifted as a whole, so the cross-term gathers of
+    // consecutive columns read consecutive elements.  On side A they take the
+    // low bits: consecutive rows then differ at the cut sites and a row group
+    // often shares cross-term source rows.
+    std::vector<char> atCut(n, 0);
+    for (int b = 0; b < nb; ++b) {
+      const int i = m->bi[b], j = m->bj[b];
+      if (((m->cut_mask >> i) & 1ULL) != ((m->cut_mask >> j) & 1ULL)) atCut[i] = atCut[j] = 1;
     }
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < n; ++i) {
+        const bool inA = (m->cut_mask >> i) & 1ULL;
+        if (atCut[i] != (inA ? 1 - pass : pass)) continue;
+        if (inA) { local[i] = (int)sitesA.size(); sitesA.push_back(i); sideOf[i] = 0; }
+        else { local[i] = (int)sitesB.size(); sitesB.push_back(i); sideOf[i] = 1; }
+      }
   } else {
     for (int i = 0; i < n; ++i) { sitesA.push_back(i); sitesB.push_back(i); local[i] = i; }
   }

@@ -78,13 +78,26 @@ def test_blocks_and_keys_match_oracle(edlib, oracle_mod, name):
     keys = ctx.state_keys()
     okeys = oracle_mod.sector_keys(m)
     np.testing.assert_array_equal(np.sort(keys), okeys)
-    # rows ascend within each block (combinadic order), columns too
+    # rows ascend within each block (combinadic order of the side-local bit
+    # words), columns too.  Side-local bits: on side A the sites on a
+    # cross-cut bond come first (low bits), on side B last (high bits)
+    if m.kind == "spin":
+        inA = [(m.cut_mask >> i) & 1 for i in range(m.n_sites)]
+        cut = [False] * m.n_sites
+        for i, j in m.bonds:
+            if inA[i] != inA[j]:
+                cut[i] = cut[j] = True
+        sa = [i for i in range(m.n_sites) if inA[i] and cut[i]] + [i for i in range(m.n_sites) if inA[i] and not cut[i]]
+        sb = [i for i in range(m.n_sites) if not inA[i] and not cut[i]] + [i for i in range(m.n_sites) if not inA[i] and cut[i]]
+
+        def local(k, sites):
+            return sum(((int(k) >> i) & 1) << p for p, i in enumerate(sites))
+
     for si, a, b, o in zip(s, dA, dB, off):
         blk = keys[o:o + a * b].reshape(a, b)
         if m.kind == "spin":
-            amask = np.uint64(m.cut_mask)
-            assert np.all(np.diff((blk[:, 0] & amask).astype(np.int64)) > 0)
-            assert np.all(np.diff((blk[0, :] & ~amask).astype(np.int64)) > 0)
+            assert np.all(np.diff([local(k, sa) for k in blk[:, 0]]) > 0)
+            assert np.all(np.diff([local(k, sb) for k in blk[0, :]]) > 0)
 
 
 def test_j1j2_4x8_structure(edlib):
