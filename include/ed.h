@@ -187,6 +187,31 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
                         const double* omega, int n_omega, double eta, double* G, double* a_p, double* b_p,
                         double* a_h, double* b_h, double* w_p, double* w_h, void* stream);
 
+/* Entanglement spectrum of a state across the cut (paper Sec. 3, figure
+ * "Distributed entanglement spectrum"): the eigenvalues lambda of the
+ * reduced density matrix rho_A = Tr_B |psi><psi|, whose logarithms give the
+ * spectrum xi = -log(lambda) of the entanglement Hamiltonian, resolved by the
+ * charge s of side A, with the sector weights W_s = sum_i lambda_{s,i} /
+ * sum_{s,i} lambda_{s,i}.  rho_A is block diagonal, rho_A(s) = Psi_s Psi_s^T;
+ * its nonzero eigenvalues are those of the Gram matrix of Psi_s in the
+ * smaller of d_A(s), d_B(s), formed in FP64 on the device by this library;
+ * the eigenvalues of each Gram matrix come from cuSOLVER's dense symmetric
+ * eigensolver (loaded on the first call; ED_EUNSUPPORTED without it).
+ *   psi      device FP64 vector of ctx (not normalised by the call)
+ *   lambda   host, capacity cap: for every block in ed_blocks order, its
+ *            min(d_A, d_B) eigenvalues in descending order (rounding can
+ *            leave eigenvalues of a rank-deficient block slightly negative)
+ *   n_lambda receives sum_s min(d_A(s), d_B(s)); with lambda NULL the call
+ *            only returns this count; cap smaller than it is ED_EINVAL
+ *   weight   host, one per block (nullable): ||Psi_s||^2 = trace rho_A(s),
+ *            summed on the device in FP64
+ *   entropy  host (nullable): -sum p ln p over p = lambda / sum(weight) > 0
+ * Device memory: one Gram matrix of the largest block (8 min(dA,dB)^2
+ * bytes) plus the eigensolver workspace; blocks with min(dA,dB) > 46340 are
+ * ED_EUNSUPPORTED.  Synchronises the stream. */
+ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
+                                   double* weight, double* entropy, void* stream);
+
 /* ---- batched form -------------------------------------------------------
  * Many independent single-block instances (Hubbard models with the spin
  * cut) packed into one device arena and stepped together: every kernel is

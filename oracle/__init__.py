@@ -25,5 +25,6 @@ from .ed import (  # noqa: F401
     continued_fraction,
     green_function,
     lehmann_green_function,
+    entanglement_spectrum,
     num_threads,
 )

@@ -271,6 +271,33 @@ def lanczos_gf(ctx: Context, psi0, e0: float, omega, eta: float, site: int = 0, 
     return G[0::2] + 1j * G[1::2], coeffs
 
 
+@dataclass
+class EntanglementSpectrum:
+    s: np.ndarray        # charge of side A of every block (ed_blocks order)
+    lam: list            # per block: eigenvalues of rho_A(s) = Psi_s Psi_s^T, descending
+    weight: np.ndarray   # per block: ||Psi_s||^2 (trace of rho_A(s))
+    entropy: float       # -sum p ln p of the normalised spectrum
+
+
+def entanglement_spectrum(ctx: Context, psi, stream=None) -> EntanglementSpectrum:
+    """Entanglement spectrum of ``psi`` across the cut (``ed_entanglement_spectrum``)."""
+    import torch
+
+    _check_vec(ctx, psi, "psi", torch.float64)
+    lib = L.load()
+    n = ctypes.c_int64()
+    L.check(lib.ed_entanglement_spectrum(ctx.handle, _ptr(psi), None, 0, ctypes.byref(n), None, None,
+                                         _stream_handle(stream)))
+    lam = np.zeros(max(n.value, 1))
+    s, dA, dB, _ = ctx.blocks()
+    wt = np.zeros(len(s))
+    ent = ctypes.c_double()
+    L.check(lib.ed_entanglement_spectrum(ctx.handle, _ptr(psi), lam.ctypes.data, n.value, ctypes.byref(n),
+                                         wt.ctypes.data, ctypes.addressof(ent), _stream_handle(stream)))
+    cuts = np.cumsum(np.minimum(dA, dB))[:-1]
+    return EntanglementSpectrum(s, np.split(lam[: n.value], cuts), wt, ent.value)
+
+
 class Batch:
     """Owns an ``ed_batch*`` (batched independent instances)."""
 
