@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrival rate (requests/s)")
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
     p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
+    p.add_argument("--no-entangle", action="store_true", help="skip the entanglement spectrum of the ground state")
     p.add_argument("--row-pass", default="auto", choices=["auto", "single", "staged", "push"],
                    help="pin the row pass of the headline workload (default: the library's choice)")
     return p.parse_args()
@@ -89,6 +90,48 @@ def sum_over_ranks(value: float, world: int, device: str = "cpu") -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+# FP64 peak of this GPU: the nominal dense figure, 1.25 TFLOP/s.  The own
+# pipe microbenchmark (`bench.py --pipes`) reads 0.505 T FMA/s = 1.01 TFLOP/s,
+# which the Gram kernel exceeds, so the nominal figure is the denominator.
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def entanglement_section(ed, ctx):
+    """Ground state (mixed precision, FP64 vector), then its entanglement
+    spectrum across the cut: time, the Gram kernels' FP64 rate against the
+    FP64 peak, sector weights W_q and the effective numbers of sectors
+    1 / sum_q w_q^2 (by weight and by block dimension)."""
+    import torch
+
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = ed.lanczos_ground(ctx, mode="mixed", tol=1e-12, psi0=psi)
+    torch.cuda.synchronize()
+    t_gs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    es = ed.entanglement_spectrum(ctx, psi)
+    t_es = time.perf_counter() - t0
+    s, dA, dB, _ = ctx.blocks()
+    m = np.minimum(dA, dB).astype(np.float64)
+    L = np.maximum(dA, dB).astype(np.float64)
+    macs = float(np.sum(m * (m + 1) / 2 * L))  # lower triangle with the diagonal
+    gram_ms, eig_ms = es.stage_ms
+    tot = float(es.weight.sum())
+    W = es.weight / tot
+    w_dim = (dA * dB) / float(np.sum(dA * dB))
+    xi_low = [float(-np.log(l[0] / tot)) if len(l) and l[0] > 0 else None for l in es.lam]
+    achieved = 2 * macs / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
+    peak = FP64_TFLOPS_NOMINAL
+    return {"ground_state_s": t_gs, "e0": r.e0, "seconds": t_es, "gram_ms": gram_ms, "eigensolver_ms": eig_ms,
+            "gram_roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                              "frac": achieved / peak if achieved else None, "flops": 2 * macs,
+                              "peak_source": "nominal FP64 dense (no measured FP64 peak in MEASURED_PEAKS.json)"},
+            "entropy": es.entropy, "s": [int(v) for v in s], "W_q": [float(v) for v in W],
+            "xi_lowest_per_sector": xi_low, "n_eff_weights": float(1.0 / np.sum(W ** 2)),
+            "n_eff_dims": float(1.0 / np.sum(w_dim ** 2)), "levels": int(sum(len(l) for l in es.lam))}
 
 
 def kernel_source_hash():
@@ -520,6 +563,15 @@ def main():
         lanczos["mixed_vs_f64_rel"] = abs(lanczos["mixed"]["e0"] - lanczos["f64"]["e0"]) / abs(lanczos["f64"]["e0"])
         lanczos["speedup_mixed"] = lanczos["f64"]["seconds"] / lanczos["mixed"]["seconds"]
 
+    # entanglement spectrum of the ground state across the cut
+    entangle = None
+    if not args.no_entangle and rank == 0:
+        torch.cuda.empty_cache()
+        try:
+            entangle = entanglement_section(ed, ctx)
+        except Exception as exc:
+            entangle = {"error": str(exc)}
+
     batched = served = None
     if not args.no_batched:
         torch.cuda.empty_cache()
@@ -559,7 +611,8 @@ def main():
                            "setup_s": t_setup, "row_pass": ctx.row_pass(tdt)},
                 "gpu_launches": args.steps * (4 if args.dtype == "f64" else 2),
                 "roofline": roof, "clocks": clk, "e2e": e2e, "other_precision": other, "lanczos": lanczos,
-                "batched": batched, "serving": served, "configs": configs, "cpu_baseline": cpu}
+                "entanglement": entangle, "batched": batched, "serving": served, "configs": configs,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

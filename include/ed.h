@@ -206,11 +206,13 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  *   weight   host, one per block (nullable): ||Psi_s||^2 = trace rho_A(s),
  *            summed on the device in FP64
  *   entropy  host (nullable): -sum p ln p over p = lambda / sum(weight) > 0
+ *   stage_ms host (nullable), 2 doubles: device time of the Gram kernels and
+ *            of the eigensolver, summed over the blocks (CUDA events)
  * Device memory: one Gram matrix of the largest block (8 min(dA,dB)^2
  * bytes) plus the eigensolver workspace; blocks with min(dA,dB) > 46340 are
  * ED_EUNSUPPORTED.  Synchronises the stream. */
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
-                                   double* weight, double* entropy, void* stream);
+                                   double* weight, double* entropy, double* stage_ms, void* stream);
 
 /* ---- batched form -------------------------------------------------------
  * Many independent single-block instances (Hubbard models with the spin

@@ -148,13 +148,22 @@ struct Handle {
   }
 };
 
+struct Events {
+  cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+  ~Events() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
 }  // namespace
 }  // namespace edk
 
 using namespace edk;
 
 extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, double* lambda, int64_t cap,
-                                              int64_t* n_lambda, double* weight, double* entropy, void* stream) {
+                                              int64_t* n_lambda, double* weight, double* entropy, double* stage_ms,
+                                              void* stream) {
   if (!c || !n_lambda) {
     set_error("ctx or n_lambda is NULL");
     return ED_EINVAL;
@@ -208,6 +217,9 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
 
   std::vector<double> w(mmax);
   std::vector<double> wt(c->blocks.size());
+  Events ev;
+  for (cudaEvent_t& x : ev.e) ED_CUDA_TRY(cudaEventCreate(&x));
+  double t_gram = 0.0, t_eig = 0.0;
   int64_t pos = 0;
   for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
     const Block& b = c->blocks[bi];
@@ -218,8 +230,10 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     const long long si = rows ? b.dB : 1, sl = rows ? 1 : b.dB, L = rows ? b.dB : b.dA;
     const int T = (m + kGT - 1) / kGT;
     const long long tiles = (long long)T * (T + 1) / 2;
+    ED_CUDA_TRY(cudaEventRecord(ev.e[0], st));
     k_gram<<<(unsigned)tiles, 256, 0, st>>>(xb, si, sl, m, L, G, T);
     ED_CUDA_TRY(cudaGetLastError());
+    ED_CUDA_TRY(cudaEventRecord(ev.e[1], st));
     int lw = 0;
     if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, G, m, W, &lw) !=
             CUSOLVER_STATUS_SUCCESS ||
@@ -232,18 +246,28 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
       set_error("cuSOLVER eigensolver failed on block %zu (dimension %d)", bi, m);
       return ED_ECUDA;
     }
+    ED_CUDA_TRY(cudaEventRecord(ev.e[2], st));
     int hinfo = 0;
     ED_CUDA_TRY(cudaMemcpyAsync(w.data(), W, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
     ED_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
     // ||Psi_s||^2 (the trace of rho_A(s)) with the library's FP64 reduction
     ED_TRY(dot_dev<double>(c, xb, xb, b.dA * b.dB, slot(c, 3), st, 0));
     ED_TRY(read_scalars(c, 3, 1, &wt[bi], st));  // synchronises the stream
+    float t1 = 0.f, t2 = 0.f;
+    ED_CUDA_TRY(cudaEventElapsedTime(&t1, ev.e[0], ev.e[1]));
+    ED_CUDA_TRY(cudaEventElapsedTime(&t2, ev.e[1], ev.e[2]));
+    t_gram += t1;
+    t_eig += t2;
     if (hinfo != 0) {
       set_error("cuSOLVER eigensolver reported info=%d on block %zu", hinfo, bi);
       return ED_ECUDA;
     }
     for (int i = 0; i < m; ++i) lambda[pos + i] = w[m - 1 - i];  // descending
     pos += m;
+  }
+  if (stage_ms) {
+    stage_ms[0] = t_gram;
+    stage_ms[1] = t_eig;
   }
   double tot = 0.0;
   for (double v : wt) tot += v;

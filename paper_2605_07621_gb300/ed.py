@@ -277,6 +277,7 @@ class EntanglementSpectrum:
     lam: list            # per block: eigenvalues of rho_A(s) = Psi_s Psi_s^T, descending
     weight: np.ndarray   # per block: ||Psi_s||^2 (trace of rho_A(s))
     entropy: float       # -sum p ln p of the normalised spectrum
+    stage_ms: tuple      # device ms of the Gram kernels and of the eigensolver
 
 
 def entanglement_spectrum(ctx: Context, psi, stream=None) -> EntanglementSpectrum:
@@ -286,16 +287,18 @@ def entanglement_spectrum(ctx: Context, psi, stream=None) -> EntanglementSpectru
     _check_vec(ctx, psi, "psi", torch.float64)
     lib = L.load()
     n = ctypes.c_int64()
-    L.check(lib.ed_entanglement_spectrum(ctx.handle, _ptr(psi), None, 0, ctypes.byref(n), None, None,
+    L.check(lib.ed_entanglement_spectrum(ctx.handle, _ptr(psi), None, 0, ctypes.byref(n), None, None, None,
                                          _stream_handle(stream)))
     lam = np.zeros(max(n.value, 1))
     s, dA, dB, _ = ctx.blocks()
     wt = np.zeros(len(s))
     ent = ctypes.c_double()
+    ms = np.zeros(2)
     L.check(lib.ed_entanglement_spectrum(ctx.handle, _ptr(psi), lam.ctypes.data, n.value, ctypes.byref(n),
-                                         wt.ctypes.data, ctypes.addressof(ent), _stream_handle(stream)))
+                                         wt.ctypes.data, ctypes.addressof(ent), ms.ctypes.data,
+                                         _stream_handle(stream)))
     cuts = np.cumsum(np.minimum(dA, dB))[:-1]
-    return EntanglementSpectrum(s, np.split(lam[: n.value], cuts), wt, ent.value)
+    return EntanglementSpectrum(s, np.split(lam[: n.value], cuts), wt, ent.value, (float(ms[0]), float(ms[1])))
 
 
 class Batch:

@@ -103,10 +103,10 @@ def test_unnormalised_input_and_errors(ed, oracle_mod):
     lib = L.load()
     n = ctypes.c_int64()
     assert lib.ed_entanglement_spectrum(ctx.handle, ctypes.c_void_p(x.data_ptr()), None, 0, ctypes.byref(n), None,
-                                        None, None) == 0
+                                        None, None, None) == 0
     s, dA, dB, _ = ctx.blocks()
     assert n.value == int(np.minimum(dA, dB).sum())
     buf = np.zeros(n.value)
     st = lib.ed_entanglement_spectrum(ctx.handle, ctypes.c_void_p(x.data_ptr()), buf.ctypes.data, n.value - 1,
-                                      ctypes.byref(n), None, None, None)
+                                      ctypes.byref(n), None, None, None, None)
     assert st == L.ED_EINVAL
