@@ -309,7 +309,7 @@ def other_configs(ed):
     ctx = ed.build_local_ops(ed.build_sectors(W.config_heis16()))
     r, dt = timed(lambda: ed.lanczos_ground(ctx, mode="f64", max_iter=150, fixed_iter=True))
     out["heis16"] = {"states": ctx.dim, "e0_150": r.e0, "seconds_150_steps": dt, "us_per_step": 1e6 * dt / 150}
-    for name, n_om, n_it in (("hub12", 2048, 300), ("hub4x4", 4096, 400)):
+    for name, n_om, n_it in (("hub12", 2048, 300), ("hub4x4", 4096, 400), ("qim15", 2048, 300)):
         m = W.config_by_name(name)
         ctx = ed.build_local_ops(ed.build_sectors(m))
         rec = {"states": ctx.dim}

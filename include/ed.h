@@ -176,9 +176,11 @@ ed_status ed_lanczos_ground(ed_ctx* ctx, const ed_lanczos_opts* opts, double* e0
  *   G(w) = <psi0| c (z - (H - E0))^-1 c^dag |psi0> + <psi0| c^dag (z + (H - E0))^-1 c |psi0>,
  * z = w + i eta, c = c_{site,spin} (spin 0 = up), from n_iter-step FP64
  * Lanczos continued fractions started from c^dag psi0 and c psi0 (built on
- * the device in the shifted sectors), fully re-orthogonalised when all
- * n_iter+1 basis vectors fit in half of the free device memory, plain
- * three-term recurrences otherwise.  psi0: device FP64 ground state of
+ * the device in the shifted sectors), fully re-orthogonalised when the
+ * shifted sector has at most 2^22 states and all n_iter+1 basis vectors fit
+ * in half of the free device memory, plain three-term recurrences otherwise
+ * (above that size the FP64 re-orthogonalisation costs many times the
+ * H|psi> of a step).  psi0: device FP64 ground state of
  * ctx; omega: host, n_omega; G: host, 2*n_omega doubles (re, im pairs).
  * a_p, b_p, a_h, b_h: optional host outputs (n_iter each) of the particle
  * and hole coefficients; w_p, w_h: optional norms ||c^dag psi0||^2,

@@ -755,6 +755,35 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
 
 // exact fixed-point FP64 apply with explicit scratch: `fixed` holds D
 // 64-bit integers, `emax` one int (cleared here before use)
+// y += V x in FP64 after the integer passes of a split diagonal: per
+// element the side diagonals, the constant and the weighted popcounts of
+// the packed cut words (PF64::diag), one CTA per row, grid-stride
+__global__ void __launch_bounds__(256) k_diag_add(P3 p, const double* __restrict__ x, double* __restrict__ y) {
+  const Dev3& t = p.t;
+  for (long long r = blockIdx.x; r < p.n_rows; r += gridDim.x) {
+    const int bi = find_blk(p.row_start, p.nblk, r);
+    const DevBlock bl = p.blocks[bi];
+    const long long a = r - p.row_start[bi];
+    const long long gA = bl.gA0 + a;
+    const unsigned pa = t.A_pack[gA];
+    const long long base = bl.off + a * bl.dB;
+    for (long long b = threadIdx.x; b < bl.dB; b += blockDim.x) {
+      const long long gB = bl.gB0 + b;
+      const unsigned pb = t.B_pack[gB];
+      const unsigned z = t.vab_and ? (pa & pb) : (pa ^ pb);
+      y[base + b] = fma(PF64::diag(t, gA, gB, z), x[base + b], y[base + b]);
+    }
+  }
+}
+
+static ed_status diag_add(ed_ctx* c, const double* x, double* y, cudaStream_t st) {
+  if (!c->diag_split || c->n_rows < 1) return ED_OK;
+  const long long g = std::min<long long>(c->n_rows, (long long)n_sms(c->device) * 16);
+  k_diag_add<<<(unsigned)g, 256, 0, st>>>(make_p3(c), x, y);
+  ED_CUDA_TRY(cudaGetLastError());
+  return ED_OK;
+}
+
 static ed_status apply_fixed(ed_ctx* c, const double* x, double* y, long long* fixed, int* emax, cudaStream_t st,
                              ProfMarks& pm) {
   const long long n = c->D;
@@ -766,12 +795,13 @@ static ed_status apply_fixed(ed_ctx* c, const double* x, double* y, long long* f
   pm.mark(1, st);
   k_to_fixed<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>(x, fixed, n, emax, c->t3.P);
   ED_CUDA_TRY(cudaGetLastError());
-  return run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm);
+  ED_TRY(run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm));
+  return diag_add(c, x, y, st);
 }
 
 bool fixed_path(const ed_ctx* c, const void* x) { return c->dyadic && v3_usable(c, ED_F64, x); }
 
-ed_status apply_prepared_fixed(ed_ctx* c, double* y, cudaStream_t st) {
+ed_status apply_prepared_fixed(ed_ctx* c, const double* x, double* y, cudaStream_t st) {
   if (!c->d_fixed) {
     set_error("fixed-point input was not prepared");
     return ED_EINVAL;
@@ -780,7 +810,8 @@ ed_status apply_prepared_fixed(ed_ctx* c, double* y, cudaStream_t st) {
   pm.begin(c);
   pm.mark(0, st);
   pm.mark(1, st);
-  const ed_status r = run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st, pm);
+  ed_status r = run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st, pm);
+  if (r == ED_OK) r = diag_add(c, x, y, st);
   pm.mark(4, st);
   pm.end(c);
   return r;

@@ -52,6 +52,8 @@ constexpr double kVecResid = 1e-10;
 // hands over, and the FP64 refinement's convergence-check interval
 constexpr double kLowResid = 3e-6;
 constexpr int kRefineCheck = 3;
+// Green's function runs re-orthogonalise only sectors up to this size
+constexpr long long kGfReorthStates = 1ll << 22;
 
 // Lanczos basis kept on the device as one contiguous array of `cap`
 // vectors (same type as the recurrence, or BF16 when only a restart vector
@@ -159,7 +161,7 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   for (int j = 0; j < max_iter && !done; ++j) {
     if constexpr (std::is_same<T, double>::value) {
       if (prepared)
-        ED_TRY(apply_prepared_fixed(c, w, st));
+        ED_TRY(apply_prepared_fixed(c, v, w, st));
       else
         ED_TRY(apply_H_impl(c, v, w, dtype_of<T>(), st));
     } else {
@@ -585,13 +587,17 @@ extern "C" ed_status ed_lanczos_gf(ed_ctx* c, const void* psi0, double e0, int s
     ED_TRY(read_scalars(c2, 3, 1, &w0, st));
     if (!(w0 > 0.0)) continue;
     launch_scale_cvt<double, double>(c2, phi, phi, 1.0 / std::sqrt(w0), n2, st);
-    // full reorthogonalisation whenever the Krylov basis fits in half of the
-    // free device memory; otherwise the plain three-term recurrence
+    // full reorthogonalisation for sectors of at most kGfReorthStates states
+    // whose Krylov basis fits in half of the free device memory; otherwise
+    // the plain three-term recurrence.  Classical Gram-Schmidt twice costs
+    // about 4 j n FP64 FMAs at step j on the slow FP64 pipe and reads the
+    // basis four times, so above a few million states it outweighs H|psi>
+    // many times (41 M states, 300 steps: 24 s against 2.5 s)
     const int steps = (int)std::min<long long>(n_iter, n2);
     Basis B;
     // (a partial basis would only re-orthogonalise the first steps, at O(j n)
     // cost each, so it is used only when every step's vector fits)
-    const bool ro = steps <= kMaxBasis &&
+    const bool ro = steps <= kMaxBasis && n2 <= kGfReorthStates &&
                     (size_t)(steps + 1) * (size_t)n2 * sizeof(double) <= free_device_bytes() / 2 &&
                     B.init(BASIS_SAME, sizeof(double), n2, steps + 1, free_device_bytes() / 2) && B.cap >= steps + 1;
     RunOut r;

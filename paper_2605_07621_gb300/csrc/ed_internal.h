@@ -222,6 +222,8 @@ struct ed_ctx {
   // class-sorted path
   bool v3_ok = false;                // tables below are valid
   bool dyadic = false;               // FP64 apply may use exact fixed point
+  bool diag_split = false;           // ... for the off-diagonal terms only; the
+                                     // diagonal is added in FP64 afterwards
   edk::Dev3 t3{};
   long long* d_fixed = nullptr;      // fixed-point copy of x (lazily allocated, D entries)
   int* d_exp = nullptr;              // exponent scratch of the fixed-point path

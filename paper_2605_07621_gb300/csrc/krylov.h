@@ -39,8 +39,9 @@ void launch_lz_b_emax(ed_ctx* c, double* w, const double* v, long long n, int* e
 void launch_lz_c_fixed(ed_ctx* c, const double* w, double* out, long long* X, const int* ew, int* ex, long long n,
                        cudaStream_t st);
 // H|psi> of the exact fixed-point path from an input already converted
-// (c->d_fixed with the scale in c->d_exp[0]); y receives FP64
-ed_status apply_prepared_fixed(ed_ctx* c, double* y, cudaStream_t st);
+// (c->d_fixed with the scale in c->d_exp[0]); y receives FP64.  x is the
+// FP64 input itself (read only when the diagonal is added in FP64)
+ed_status apply_prepared_fixed(ed_ctx* c, const double* x, double* y, cudaStream_t st);
 // the fixed-point FP64 path applies to x on this context
 bool fixed_path(const ed_ctx* c, const void* x);
 template <typename T>

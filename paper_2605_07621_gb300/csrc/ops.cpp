@@ -174,6 +174,7 @@ bool build_side3(const HostSideOps& h, const std::vector<double>& cls_val, Side3
 static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& hb) {
   c->v3_ok = false;
   c->dyadic = false;
+  c->diag_split = false;
   if (c->cross.size() > 32) return ED_OK;
   if (c->kind == ED_HUBBARD && c->n_sites > 32) return ED_OK;
   for (const Block& b : c->blocks)
@@ -237,16 +238,29 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
     for (size_t g = 0; ok && g < hb.diag.size(); ++g) ok = dyadic_at(hb.diag[g], k);
     if (ok) qs = k;
   }
+  // otherwise, when only the diagonal is not dyadic (disordered on-site
+  // energies, say), the integer passes take the off-diagonal terms and the
+  // diagonal is added in FP64 after them (one FMA per element)
+  c->diag_split = false;
+  for (int k = 0; qs < 0 && k <= 30; ++k) {
+    bool ok = true;
+    for (double v : cls) ok = ok && dyadic_at(v, k);
+    if (ok) {
+      qs = k;
+      c->diag_split = true;
+    }
+  }
   if (qs >= 0) {
     t.q_shift = qs;
     for (size_t i = 0; i < cls.size(); ++i) t.wI[i] = (long long)std::ldexp(cls[i], qs);
     for (size_t k = 0; k < c->cross.size(); ++k) t.bond_wI[k] = (long long)std::ldexp(c->cross[k].coef, qs);
-    for (int q = 0; q < dp.ncls; ++q) t.dwI[q] = (long long)std::ldexp(dp.w[q], qs);
-    t.dc0_I = (long long)std::ldexp(dp.c0, qs);
-    a3.dI.resize(ha.diag.size());
-    b3.dI.resize(hb.diag.size());
-    for (size_t g = 0; g < ha.diag.size(); ++g) a3.dI[g] = (int)std::ldexp(ha.diag[g], qs);
-    for (size_t g = 0; g < hb.diag.size(); ++g) b3.dI[g] = (int)std::ldexp(hb.diag[g], qs);
+    const bool sd = c->diag_split;  // diagonal tables of the integer passes stay zero
+    for (int q = 0; q < dp.ncls; ++q) t.dwI[q] = sd ? 0 : (long long)std::ldexp(dp.w[q], qs);
+    t.dc0_I = sd ? 0 : (long long)std::ldexp(dp.c0, qs);
+    a3.dI.assign(ha.diag.size(), 0);
+    b3.dI.assign(hb.diag.size(), 0);
+    for (size_t g = 0; !sd && g < ha.diag.size(); ++g) a3.dI[g] = (int)std::ldexp(ha.diag[g], qs);
+    for (size_t g = 0; !sd && g < hb.diag.size(); ++g) b3.dI[g] = (int)std::ldexp(hb.diag[g], qs);
     // bound on sum_j |M_ij| (units 2^-q_shift) -> headroom of the int64 sums
     auto side_max = [&](const Side3& s3, const std::vector<int>& dI) {
       double m = 0.0;
@@ -259,11 +273,13 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
     };
     double rmax = side_max(a3, a3.dI) + side_max(b3, b3.dI) + std::fabs((double)t.dc0_I);
     for (int q = 0; q < dp.ncls; ++q) rmax += std::fabs((double)t.dwI[q]) * __builtin_popcountll(dp.mask[q]);
+    // (the diagonal terms of a split diagonal are zero here: dI, dwI, dc0_I)
     for (size_t k = 0; k < c->cross.size(); ++k) rmax += std::fabs((double)t.wI[c->cross_cls[k]]);
     int bits = (int)std::ceil(std::log2(rmax + 1.0));
     t.P = std::min(60, 62 - bits);
     c->dyadic = t.P >= 40;
   }
+  if (!c->dyadic) c->diag_split = false;
   // upload
   uint2 *Am, *Bm;
   uint16_t *Ac, *Bc, *mA, *mB;

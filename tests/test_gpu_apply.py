@@ -47,6 +47,14 @@ def _models():
         "hub_rect_dyadic": W.hubbard_torus(2, 4, 1.0, 2.0, 3, 5),
         "hub_site_U": W.Model("hubbard", 5, W.chain_bonds(5, True), t=1.0, U=[1.0, 2.0, 3.0, 1.0, 0.0],
                               eps=[0.1, -0.2, 0.3, 0.0, 0.5], n_up=2, n_dw=3, spin_cut=True),
+        # Anderson impurity (star): one dyadic hybridisation value and disordered
+        # bath energies (FP64: integer passes for the hopping, diagonal added in
+        # FP64 afterwards), and eight distinct hybridisations (more value
+        # classes than the class-sorted kernels take: the general CSR kernels).
+        # hub_site_U above also has dyadic hopping and a non-dyadic diagonal.
+        "qim_uniform_V": W.anderson_impurity(8, 3.0, -1.5, 0.5, W.impurity_bath(8, seed=11), 4, 5),
+        "qim_distinct_V": W.anderson_impurity(8, 2.0, -0.7, rng.uniform(0.2, 0.9, 8), W.impurity_bath(8, seed=12),
+                                              5, 3),
     }
 
 

@@ -72,7 +72,8 @@ def test_j1j2_4x4_ground_state(ed, oracle_mod, mask):
     _check(ed, oracle_mod, m, psi)
 
 
-@pytest.mark.parametrize("name", ["hub12", "j1j2_4x6", "xxz_odd_cut", "all_on_A", "all_on_B", "hub_empty_dw"])
+@pytest.mark.parametrize("name", ["hub12", "j1j2_4x6", "xxz_odd_cut", "all_on_A", "all_on_B", "hub_empty_dw",
+                                  "qim9"])
 def test_random_states(ed, oracle_mod, name):
     # ragged Gram tiles (924 = 14 x 64 + 28), both Gram orientations
     # (d_A < d_B and d_A > d_B), one-column and one-row blocks
@@ -81,7 +82,8 @@ def test_random_states(ed, oracle_mod, name):
          "xxz_odd_cut": W.xxz_chain(11, 1.0, 0.5, n_up=4, cut_mask=0b10110100101),
          "all_on_A": W.heisenberg_chain(10, cut_mask=0x3FF),
          "all_on_B": W.heisenberg_chain(10, cut_mask=0),
-         "hub_empty_dw": W.hubbard_chain(7, 1.0, 2.0, 3, 0)}[name]
+         "hub_empty_dw": W.hubbard_chain(7, 1.0, 2.0, 3, 0),
+         "qim9": W.anderson_impurity(8, 4.0, -2.0, 0.5, W.impurity_bath(8), 4, 5)}[name]
     _check(ed, oracle_mod, m, seed=777)
 
 

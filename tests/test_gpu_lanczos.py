@@ -176,3 +176,29 @@ def test_green_function_lehmann(ed, oracle_mod, spin, site):
     G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=site, spin=spin, n_iter=500)
     assert np.abs(G - Gref).max() < 1e-9 * np.abs(Gref).max()
     assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_impurity_ground_state(ed, oracle_mod, mode):
+    """Anderson impurity, 9 sites (15,876 states): E0 against the oracle's Lanczos."""
+    m = W.anderson_impurity(8, 4.0, -2.0, 0.5, W.impurity_bath(8, seed=21), 4, 5)
+    e_ref, _, _ = oracle_mod.ground_state(m, tol=1e-14)
+    r = ed.lanczos_ground(_ctx(ed, m), mode=mode, tol=1e-13)
+    assert r.converged and abs(r.e0 - e_ref) < 1e-10 * abs(e_ref)
+
+
+def test_impurity_green_function_lehmann(ed, oracle_mod):
+    """Impurity Green's function G_dd of a 6-site Anderson model against the
+    Lehmann sum over dense eigenpairs (Krylov space exhausted: exact)."""
+    import torch
+
+    m = W.anderson_impurity(5, 3.0, -1.0, [0.3, 0.5, 0.4, 0.6, 0.35], W.impurity_bath(5, seed=8), 3, 3)
+    omega = np.linspace(-6, 6, 241)
+    Gref, e_dense = oracle_mod.lehmann_green_function(m, omega, 0.05, site=0, spin=0)
+    ctx = _ctx(ed, m)
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(ctx, mode="f64", psi0=psi, tol=1e-14, reorth=True)
+    assert abs(r.e0 - e_dense) < 1e-11 * abs(e_dense)
+    G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=500)
+    assert np.abs(G - Gref).max() < 1e-9 * np.abs(Gref).max()
+    assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-12

@@ -166,3 +166,41 @@ def test_hubbard_spin_su2(oracle_mod):
             tmp = o.fermion_op(src, i, 1, False, ks, e, km)      # c_{i dw}
             Sp[:, j] += o.fermion_op(mid, i, 0, True, km, tmp, kd)  # c^dag_{i up}
     assert np.abs(Hd @ Sp - Sp @ Hs).max() < 1e-12
+
+
+# ---------------------------------------------------------------- Anderson impurity (star geometry)
+
+@pytest.mark.parametrize("n_up,n_dw", [(3, 3), (4, 2), (1, 5)])
+def test_impurity_atomic_limit(oracle_mod, n_up, n_dw):
+    """V = 0: impurity and bath decouple.  E0 = min over the impurity
+    occupations (nu, nd) of eps_d (nu + nd) + U nu nd plus the lowest
+    n_up - nu and n_dw - nd bath levels."""
+    eb = W.impurity_bath(5, seed=3)
+    U, ed_ = 3.0, -1.2
+    m = W.anderson_impurity(5, U, ed_, 0.0, eb, n_up, n_dw)
+    e0, _ = _dense_e0(oracle_mod, m)
+    best = min(ed_ * (nu + nd) + U * nu * nd + eb[: n_up - nu].sum() + eb[: n_dw - nd].sum()
+               for nu in (0, 1) for nd in (0, 1) if n_up - nu <= 5 and n_dw - nd <= 5)
+    assert abs(e0 - best) < 1e-12
+
+
+def test_impurity_free_fermions(oracle_mod):
+    """U = 0: Slater determinants of the star's one-body levels (distinct V_k)."""
+    rng = np.random.default_rng(7)
+    m = W.anderson_impurity(6, 0.0, 0.3, rng.uniform(0.2, 0.8, 6), W.impurity_bath(6, seed=5), 3, 4)
+    eps = _one_body(m)
+    e0, _ = _dense_e0(oracle_mod, m)
+    assert abs(e0 - (eps[:3].sum() + eps[:4].sum())) < 1e-12
+
+
+def test_impurity_single_bath_site_closed_form(oracle_mod):
+    """One bath orbital at energy 0, one electron of each spin, eps_d = -U/2.
+    The configurations with one electron on each site have energy -U/2; the
+    doubly occupied and the empty impurity have energy 0.  V couples the
+    spin-singlet combination of the former to the symmetric combination of
+    the latter with matrix element 2V (the triplet stays at -U/2), so
+    E0 = (-U/2 - sqrt(U^2/4 + 16 V^2)) / 2."""
+    for U, V in ((2.0, 0.7), (6.0, 0.3), (0.0, 1.1)):
+        m = W.anderson_impurity(1, U, -U / 2, V, [0.0], 1, 1)
+        e0, _ = _dense_e0(oracle_mod, m)
+        assert abs(e0 - (-U / 2 - np.sqrt(U * U / 4 + 16 * V * V)) / 2) < 1e-13

@@ -19,12 +19,15 @@ from .lattices import (  # noqa: F401
     hubbard_torus,
     hubbard_open_cluster,
     hubbard_dimer,
+    anderson_impurity,
+    impurity_bath,
     batched_hubbard_instances,
     config_heis16,
     config_hub12,
     config_j1j2_4x8,
     config_hub4x4,
     config_j1j2_4x7,
+    config_qim15,
     CONFIG_NAMES,
     config_by_name,
 )

@@ -250,6 +250,39 @@ def hubbard_dimer(t: float = 1.0, U: float = 4.0) -> Model:
     return Model("hubbard", 2, [(0, 1)], t=t, U=U, n_up=1, n_dw=1, spin_cut=True, name="hubbard_dimer")
 
 
+def anderson_impurity(n_bath: int, U: float, eps_d: float, V, eps_bath, n_up: int, n_dw: int) -> Model:
+    """Single-impurity Anderson model in the star geometry: site 0 is the
+    impurity (energy eps_d, interaction U), sites 1..n_bath the bath orbitals
+    (energies eps_bath, no interaction), each coupled to the impurity by the
+    hybridisation V_k (scalar or one per bath site):
+        H = sum_s eps_d n_0s + U n_0u n_0d + sum_{k,s} eps_k n_ks
+            + sum_{k,s} V_k (c^dag_0s c_ks + h.c.).
+    In this package's Hubbard convention (-t per bond) the bonds carry t = -V_k.
+    The cut is the spin cut (A = up electrons, B = down electrons).
+    """
+    Vk = np.broadcast_to(np.asarray(V, dtype=np.float64), (n_bath,))
+    eb = np.asarray(eps_bath, dtype=np.float64)
+    if eb.shape != (n_bath,):
+        raise ValueError("eps_bath needs one energy per bath site")
+    S = n_bath + 1
+    bonds = [(0, k) for k in range(1, S)]
+    Us = np.zeros(S)
+    Us[0] = U
+    eps = np.concatenate([[eps_d], eb])
+    return Model("hubbard", S, bonds, t=[-float(v) for v in Vk], U=Us, eps=eps, n_up=n_up, n_dw=n_dw,
+                 spin_cut=True, name=f"anderson_impurity_{n_bath}")
+
+
+def impurity_bath(n_bath: int, half_width: float = 2.0, seed: int = 20260507) -> np.ndarray:
+    """Particle-hole symmetric bath energies: n_bath // 2 seeded values
+    U[0.05, half_width] and their negatives (a zero level when n_bath is odd),
+    in ascending order."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(0.05, half_width, size=n_bath // 2)
+    out = np.concatenate([-e, e, [0.0] * (n_bath % 2)])
+    return np.sort(out)
+
+
 def batched_hubbard_instances(n: int = 512, seed: int = 20260507) -> List[Model]:
     """The batched workload: independent Hubbard instances with a spin cut.
 
@@ -322,9 +355,19 @@ def config_j1j2_4x7() -> Model:
     return m
 
 
-CONFIG_NAMES = ("heis16", "hub12", "j1j2_4x8", "hub4x4", "j1j2_4x7")
+def config_qim15() -> Model:
+    """Anderson impurity with 14 bath orbitals (S = 15 sites), U = 4 at the
+    impurity, eps_d = -U/2, V = 0.5 to every bath orbital, particle-hole
+    symmetric seeded bath on [-2, 2]; N_up = 8, N_dw = 7 (6435 x 6435 =
+    41,409,225 states), spin cut."""
+    m = anderson_impurity(14, 4.0, -2.0, 0.5, impurity_bath(14), 8, 7)
+    m.name = "qim15"
+    return m
+
+
+CONFIG_NAMES = ("heis16", "hub12", "j1j2_4x8", "hub4x4", "j1j2_4x7", "qim15")
 
 
 def config_by_name(name: str) -> Model:
     return {"heis16": config_heis16, "hub12": config_hub12, "j1j2_4x8": config_j1j2_4x8,
-            "hub4x4": config_hub4x4, "j1j2_4x7": config_j1j2_4x7}[name]()
+            "hub4x4": config_hub4x4, "j1j2_4x7": config_j1j2_4x7, "qim15": config_qim15}[name]()
