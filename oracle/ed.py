@@ -17,6 +17,9 @@ use this module.  It never touches the CUDA path.
   c|psi0> (the paper only names dynamical correlations; this definition is
   the standard zero-temperature one).  ``lehmann_green_function`` gives the
   same quantity as a sum over dense eigenpairs.
+* Entanglement spectrum: the eigenvalues of rho_A = Tr_B |psi><psi| per
+  charge of side A, as squared singular values of the blocks Psi_s[a, b]
+  built from the full-sector keys (``entanglement_spectrum``).
 """
 from __future__ import annotations
 
