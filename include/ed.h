@@ -176,18 +176,28 @@ ed_status ed_lanczos_ground(ed_ctx* ctx, const ed_lanczos_opts* opts, double* e0
  *   G(w) = <psi0| c (z - (H - E0))^-1 c^dag |psi0> + <psi0| c^dag (z + (H - E0))^-1 c |psi0>,
  * z = w + i eta, c = c_{site,spin} (spin 0 = up), from n_iter-step FP64
  * Lanczos continued fractions started from c^dag psi0 and c psi0 (built on
- * the device in the shifted sectors), fully re-orthogonalised when the
- * shifted sector has at most 2^22 states and all n_iter+1 basis vectors fit
- * in half of the free device memory, plain three-term recurrences otherwise
- * (above that size the FP64 re-orthogonalisation costs many times the
- * H|psi> of a step).  psi0: device FP64 ground state of
+ * the device in the shifted sectors).  reorth selects how the Krylov
+ * vectors are kept orthogonal (ED_GF_REORTH_*): FULL orthogonalises every
+ * step against the whole basis (classical Gram-Schmidt twice); PARTIAL only
+ * the steps at which the estimated loss of orthogonality (Simon's
+ * recurrence) reaches sqrt(eps), and the step after; both need all n_iter+1
+ * basis vectors in half of the free device memory (ED_ENOMEM otherwise).
+ * AUTO: FULL for shifted sectors of at most 2^22 states, PARTIAL above, and
+ * the plain three-term recurrence when the basis does not fit (above that
+ * size full orthogonalisation costs many times the H|psi> of a step).  psi0: device FP64 ground state of
  * ctx; omega: host, n_omega; G: host, 2*n_omega doubles (re, im pairs).
  * a_p, b_p, a_h, b_h: optional host outputs (n_iter each) of the particle
  * and hole coefficients; w_p, w_h: optional norms ||c^dag psi0||^2,
  * ||c psi0||^2.  Synchronises the stream. */
+enum {
+  ED_GF_REORTH_AUTO = -1,   /* full up to 2^22 states, partial above (when the basis fits) */
+  ED_GF_REORTH_NONE = 0,    /* plain three-term recurrence */
+  ED_GF_REORTH_FULL = 1,    /* every step against the whole basis */
+  ED_GF_REORTH_PARTIAL = 2  /* when the estimated loss of orthogonality reaches sqrt(eps) */
+};
 ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int spin, int n_iter,
                         const double* omega, int n_omega, double eta, double* G, double* a_p, double* b_p,
-                        double* a_h, double* b_h, double* w_p, double* w_h, void* stream);
+                        double* a_h, double* b_h, double* w_p, double* w_h, int reorth, void* stream);
 
 /* Entanglement spectrum of a state across the cut (paper Sec. 3, figure
  * "Distributed entanglement spectrum"): the eigenvalues lambda of the

@@ -68,7 +68,8 @@ SIGNATURES = [
     ("ed_lanczos_default_opts", None, [P(LanczosOpts)]),
     ("ed_lanczos_ground", c_int, [c_void_p, P(LanczosOpts), P(c_double), c_void_p, P(Report)]),
     ("ed_lanczos_gf", c_int, [c_void_p, c_void_p, c_double, c_int, c_int, c_int, c_void_p, c_int, c_double,
-                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                              c_void_p]),
     ("ed_entanglement_spectrum", c_int, [c_void_p, c_void_p, c_void_p, c_int64, P(c_int64), c_void_p, c_void_p,
                                          c_void_p, c_void_p]),
     ("ed_batch_create", c_int, [c_void_p, c_int, c_int, P(c_void_p)]),

@@ -118,6 +118,7 @@ struct RunOut {
   std::vector<double> alpha, beta;  // beta[j] = beta_{j+1}
   bool converged = false;
   double theta = 0.0;
+  int orthogonalised = 0;  // steps whose vector was orthogonalised against the basis
 };
 
 // Three-term Lanczos recurrence from the normalised v0 (device, type T).
@@ -131,9 +132,60 @@ struct RunOut {
 // (on an invalid vector) are discarded, and the run ends at the breakdown.
 constexpr int kReadEvery = 16;
 
+// Partial reorthogonalisation (Simon 1984): the level of orthogonality
+// omega_{j,k} = v_j . v_k is estimated by its own recurrence, obtained by
+// projecting the three-term recurrence on v_k,
+//   b_j w_{j+1,k} = b_k w_{j,k+1} + (a_k - a_j) w_{j,k} + b_{k-1} w_{j,k-1}
+//                   - b_{j-1} w_{j-1,k}  (+ a rounding term of order eps |H|),
+// with b_j = beta_{j+1}.  When some |w_{j+1,k}| exceeds sqrt(eps) the new
+// vector, and the one after it, are orthogonalised against the whole basis
+// (classical Gram-Schmidt twice) and their estimates reset to eps.  This
+// keeps the basis semi-orthogonal, which leaves the tridiagonal matrix (and
+// so the Ritz values and continued fractions) accurate to rounding, at a
+// fraction of the cost of orthogonalising every step.
+struct OmegaPRO {
+  std::vector<double> a, b;       // alpha_k, beta_{k+1} of the steps so far
+  std::vector<double> cur, prev;  // omega_{j,k}, omega_{j-1,k}
+  bool force = false;             // orthogonalise the next vector as well
+  int count = 0;                  // steps orthogonalised
+  static constexpr double kEps = 2.220446049250313e-16;
+  // step j gave alpha_j and b_j (before any correction); true when w
+  // (the next vector) must be orthogonalised
+  bool need(double aj, double bj, double anorm) {
+    const int j = (int)a.size();
+    a.push_back(aj);
+    b.push_back(bj);
+    std::vector<double> nw(j + 2, 0.0);
+    if (j == 0) {
+      cur.assign(1, 1.0);
+    }
+    double mx = 0.0;
+    for (int k = 0; k < j && bj > 0.0; ++k) {
+      double num = b[k] * cur[k + 1] + (a[k] - aj) * cur[k] - (j > 0 ? b[j - 1] * prev[k] : 0.0);
+      if (k > 0) num += b[k - 1] * cur[k - 1];
+      num += (num >= 0.0 ? 1.0 : -1.0) * 2.0 * kEps * anorm;
+      nw[k] = num / bj;
+      mx = std::max(mx, std::fabs(nw[k]));
+    }
+    nw[j] = bj > 0.0 ? kEps * anorm / bj : kEps;
+    nw[j + 1] = 1.0;
+    prev = cur;
+    cur = nw;
+    const bool r = force || mx > std::sqrt(kEps);
+    force = r && !force;
+    return r;
+  }
+  // the vector was orthogonalised: its estimates are back at rounding level
+  void reset(double bj_new) {
+    b.back() = bj_new;
+    for (size_t k = 0; k + 1 < cur.size(); ++k) cur[k] = kEps;
+    ++count;
+  }
+};
+
 template <typename T>
 ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_iter, double tol, int check_every,
-                 bool fixed, bool reorth, Basis* basis, RunOut& out, double resid_tol = 0.0) {
+                 bool fixed, bool reorth, Basis* basis, RunOut& out, double resid_tol = 0.0, bool partial = false) {
   const long long n = c->D;
   T* vprev = bufs[0];
   T* v = bufs[1];
@@ -158,7 +210,11 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   bool fuse = false, prepared = false;
   if constexpr (std::is_same<T, double>::value) fuse = !reorth && fixed_path(c, v);
   int* ew = c->d_exp + 1;
+  const bool pro = partial && !reorth && basis && basis->kind == BASIS_SAME && basis->complete;
+  OmegaPRO om;
+  double anorm = 0.0;
   for (int j = 0; j < max_iter && !done; ++j) {
+    bool ortho_now = false;
     if constexpr (std::is_same<T, double>::value) {
       if (prepared)
         ED_TRY(apply_prepared_fixed(c, v, w, st));
@@ -181,6 +237,20 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
       for (int pass = 0; pass < 2; ++pass)
         launch_reorth<T>(c, (const T*)basis->base, n, basis->count, w, n, hcoef(c), st);
       ED_TRY(dot_dev<T>(c, w, w, n, slot(c, 1), st, 1));
+    }
+    if (pro && basis->complete && basis->count <= kMaxBasis) {
+      double ab[2];
+      ED_TRY(read_scalars(c, 0, 2, ab, st));  // alpha_j, beta_{j+1} (synchronises)
+      anorm = std::max(anorm, std::fabs(ab[0]) + ab[1]);
+      if (om.need(ab[0], ab[1], anorm)) {
+        for (int pass = 0; pass < 2; ++pass)
+          launch_reorth<T>(c, (const T*)basis->base, n, basis->count, w, n, hcoef(c), st);
+        ED_TRY(dot_dev<T>(c, w, w, n, slot(c, 1), st, 1));
+        double bn;
+        ED_TRY(read_scalars(c, 1, 1, &bn, st));
+        om.reset(bn);
+        ortho_now = true;
+      }
     }
     ED_CUDA_TRY(cudaMemcpyAsync(hist + 2 * j, slot(c, 0), 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     ED_CUDA_TRY(cudaGetLastError());
@@ -222,11 +292,13 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
     }
     if (m == max_iter) break;
     if constexpr (std::is_same<T, double>::value) {
-      if (fuse && c->d_fixed) {
+      // (after an orthogonalisation the exponent lz_b recorded may be stale)
+      if (fuse && c->d_fixed && !ortho_now) {
         launch_lz_c_fixed(c, w, vprev, c->d_fixed, ew, c->d_exp, n, st);
         prepared = true;
       } else {
         launch_lz_c<T>(c, w, vprev, n, st);
+        prepared = false;
       }
     } else {
       launch_lz_c<T>(c, w, vprev, n, st);
@@ -238,6 +310,7 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   // after a breakdown or convergence inside a read batch)
   const int steps = (int)out.alpha.size();
   out.theta = tridiag_lowest(out.alpha.data(), out.beta.data(), steps);
+  out.orthogonalised = pro ? om.count : (reorth ? steps : 0);
   if (basis && basis->count > steps) basis->count = steps;
   bufs[0] = vprev;
   bufs[1] = v;
@@ -540,8 +613,9 @@ ed_status fermion_apply(ed_ctx* c, ed_ctx* c2, const double* psi0, int site, int
 
 extern "C" ed_status ed_lanczos_gf(ed_ctx* c, const void* psi0, double e0, int site, int spin, int n_iter,
                                    const double* omega, int n_omega, double eta, double* G, double* a_p, double* b_p,
-                                   double* a_h, double* b_h, double* w_p, double* w_h, void* stream) {
+                                   double* a_h, double* b_h, double* w_p, double* w_h, int reorth, void* stream) {
   if (!c || !psi0 || (n_omega > 0 && (!omega || !G))) { set_error("NULL argument"); return ED_EINVAL; }
+  if (reorth < ED_GF_REORTH_AUTO || reorth > ED_GF_REORTH_PARTIAL) { set_error("bad reorth mode %d", reorth); return ED_EINVAL; }
   if (c->kind != ED_HUBBARD) { set_error("the Green's function needs a Hubbard context"); return ED_EINVAL; }
   if (!c->ops_built) { set_error("ed_build_local_ops has not been called"); return ED_EINVAL; }
   if (site < 0 || site >= c->n_sites || (spin != 0 && spin != 1) || n_iter < 1 || n_omega < 0 || !(eta >= 0.0)) {
@@ -587,9 +661,11 @@ extern "C" ed_status ed_lanczos_gf(ed_ctx* c, const void* psi0, double e0, int s
     ED_TRY(read_scalars(c2, 3, 1, &w0, st));
     if (!(w0 > 0.0)) continue;
     launch_scale_cvt<double, double>(c2, phi, phi, 1.0 / std::sqrt(w0), n2, st);
-    // full reorthogonalisation for sectors of at most kGfReorthStates states
-    // whose Krylov basis fits in half of the free device memory; otherwise
-    // the plain three-term recurrence.  Classical Gram-Schmidt twice costs
+    // re-orthogonalisation against the kept Krylov basis: full (every step)
+    // for sectors of at most kGfReorthStates states, partial (when the
+    // estimated loss of orthogonality reaches sqrt(eps)) above; both need
+    // the whole basis in half of the free device memory, otherwise the plain
+    // three-term recurrence runs.  Full classical Gram-Schmidt twice costs
     // about 4 j n FP64 FMAs at step j on the slow FP64 pipe and reads the
     // basis four times, so above a few million states it outweighs H|psi>
     // many times (41 M states, 300 steps: 24 s against 2.5 s)
@@ -597,11 +673,20 @@ extern "C" ed_status ed_lanczos_gf(ed_ctx* c, const void* psi0, double e0, int s
     Basis B;
     // (a partial basis would only re-orthogonalise the first steps, at O(j n)
     // cost each, so it is used only when every step's vector fits)
-    const bool ro = steps <= kMaxBasis && n2 <= kGfReorthStates &&
-                    (size_t)(steps + 1) * (size_t)n2 * sizeof(double) <= free_device_bytes() / 2 &&
-                    B.init(BASIS_SAME, sizeof(double), n2, steps + 1, free_device_bytes() / 2) && B.cap >= steps + 1;
+    const bool want = reorth != ED_GF_REORTH_NONE;
+    const bool fits = want && steps <= kMaxBasis &&
+                      (size_t)(steps + 1) * (size_t)n2 * sizeof(double) <= free_device_bytes() / 2 &&
+                      B.init(BASIS_SAME, sizeof(double), n2, steps + 1, free_device_bytes() / 2) &&
+                      B.cap >= steps + 1;
+    if (!fits && (reorth == ED_GF_REORTH_FULL || reorth == ED_GF_REORTH_PARTIAL)) {
+      set_error("the Krylov basis (%d x %lld states) does not fit in half of the free device memory", steps + 1,
+                (long long)n2);
+      return ED_ENOMEM;
+    }
+    const bool full = fits && (reorth == ED_GF_REORTH_FULL || (reorth == ED_GF_REORTH_AUTO && n2 <= kGfReorthStates));
+    const bool partial = fits && !full;
     RunOut r;
-    ED_TRY(lz_run<double>(c2, st, bufs, phi, steps, 0.0, 1, true, ro, ro ? &B : nullptr, r));
+    ED_TRY(lz_run<double>(c2, st, bufs, phi, steps, 0.0, 1, true, full, fits ? &B : nullptr, r, 0.0, partial));
     ED_CUDA_TRY(cudaStreamSynchronize(st));
     if (create) { hp_a = r.alpha; hp_b = r.beta; wp = w0; }
     else { hh_a = r.alpha; hh_b = r.beta; wh = w0; }

@@ -253,9 +253,13 @@ def lanczos_ground(ctx: Context, mode: str = "f64", max_iter: int = 400, tol: fl
                          r.residual, r.seconds, a[: r.n_ab].copy(), b[: r.n_ab].copy(), st)
 
 
+GF_REORTH = {"auto": -1, "none": 0, "full": 1, "partial": 2}
+
+
 def lanczos_gf(ctx: Context, psi0, e0: float, omega, eta: float, site: int = 0, spin: int = 0, n_iter: int = 300,
-               stream=None):
-    """G(omega + i eta) (complex numpy array) and the Lanczos coefficients."""
+               reorth: str = "auto", stream=None):
+    """G(omega + i eta) (complex numpy array) and the Lanczos coefficients.
+    reorth: "auto", "none", "full" or "partial" (``ED_GF_REORTH_*``)."""
     import torch
 
     _check_vec(ctx, psi0, "psi0", torch.float64)
@@ -266,7 +270,7 @@ def lanczos_gf(ctx: Context, psi0, e0: float, omega, eta: float, site: int = 0, 
     L.check(L.load().ed_lanczos_gf(ctx.handle, _ptr(psi0), float(e0), int(site), int(spin), int(n_iter),
                                    om.ctypes.data, len(om), float(eta), G.ctypes.data, ap.ctypes.data,
                                    bp.ctypes.data, ah.ctypes.data, bh.ctypes.data, ctypes.addressof(wp),
-                                   ctypes.addressof(wh), _stream_handle(stream)))
+                                   ctypes.addressof(wh), GF_REORTH[reorth], _stream_handle(stream)))
     coeffs = {"particle": (wp.value, ap, bp), "hole": (wh.value, ah, bh)}
     return G[0::2] + 1j * G[1::2], coeffs
 

@@ -121,7 +121,14 @@ def _cf_green(g, omega, eta, m):
             - oracle.continued_fraction(g["e0"] - z, g["w_hole"], ah, bh))
 
 
-def test_hub12_green_function(ed):
+@pytest.mark.parametrize("reorth", ["auto", "partial"])
+def test_hub12_green_function(ed, reorth):
+    """Hub12 G_00(omega) with full re-orthogonalisation (auto at this size) or
+    the partial one; the checks are those of _hub12_gf_check."""
+    _hub12_gf_check(ed, reorth)
+
+
+def _hub12_gf_check(ed, reorth):
     """Hub12 G_00(omega), 2048 frequencies on [-15, 15], 300 Lanczos steps.
 
     The oracle's coefficients (500 steps, full reorthogonalisation) are
@@ -142,7 +149,7 @@ def test_hub12_green_function(ed):
     r = ed.lanczos_ground(ctx, mode="f64", psi0=psi, tol=1e-14)
     assert abs(r.e0 - g["e0"]) <= 1e-10 * abs(g["e0"])
     omega = np.linspace(-15.0, 15.0, 2048)
-    G5, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.5, site=0, spin=0, n_iter=300)
+    G5, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.5, site=0, spin=0, n_iter=300, reorth=reorth)
     assert abs(co["particle"][0] - g["w_particle"]) < 1e-9
     assert abs(co["hole"][0] - g["w_hole"]) < 1e-9
     assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-9
@@ -153,7 +160,7 @@ def test_hub12_green_function(ed):
         assert np.abs(co[side][2][:5] - np.array(g["b_" + side][:5])).max() < 1e-9
     ref5 = _cf_green(g, omega, 0.5, 300)
     assert np.abs(G5 - ref5).max() <= 1e-9 * np.abs(ref5).max()
-    G05, _ = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=300)
+    G05, _ = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=300, reorth=reorth)
     ref300 = _cf_green(g, omega, 0.05, 300)
     spread = np.abs(ref300 - _cf_green(g, omega, 0.05, 500)).max()
     assert np.abs(G05 - ref300).max() <= 2.0 * spread
@@ -202,3 +209,29 @@ def test_impurity_green_function_lehmann(ed, oracle_mod):
     G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=500)
     assert np.abs(G - Gref).max() < 1e-9 * np.abs(Gref).max()
     assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-12
+
+
+def test_green_function_plain_recurrence_and_modes(ed):
+    """Without re-orthogonalisation the well-conditioned quantities stay exact
+    (weights, sum rule, first coefficients) and G stays causal; an unknown
+    mode is rejected."""
+    import ctypes
+
+    import torch
+
+    from paper_2605_07621_gb300 import _lib as L
+
+    g = _gold("hub12.json")
+    ctx = _ctx(ed, W.config_hub12())
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(ctx, mode="f64", psi0=psi, tol=1e-14)
+    omega = np.linspace(-15.0, 15.0, 512)
+    G, co = ed.lanczos_gf(ctx, psi, r.e0, omega, 0.05, site=0, spin=0, n_iter=300, reorth="none")
+    assert abs(co["particle"][0] + co["hole"][0] - 1.0) < 1e-9
+    for side in ("particle", "hole"):
+        assert np.abs(co[side][1][:5] - np.array(g["a_" + side][:5])).max() < 1e-9
+    assert G.imag.max() <= 0.0
+    Gr = np.zeros(2 * len(omega))
+    st = L.load().ed_lanczos_gf(ctx.handle, ctypes.c_void_p(psi.data_ptr()), r.e0, 0, 0, 10, omega.ctypes.data,
+                                len(omega), 0.05, Gr.ctypes.data, None, None, None, None, None, None, 7, None)
+    assert st == L.ED_EINVAL
