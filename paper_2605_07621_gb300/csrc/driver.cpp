@@ -52,6 +52,9 @@ constexpr double kVecResid = 1e-10;
 // hands over, and the FP64 refinement's convergence-check interval
 constexpr double kLowResid = 3e-6;
 constexpr int kRefineCheck = 3;
+// Lanczos runs on sectors up to this size replay pairs of steps from a
+// captured CUDA graph (their steps are bound by launch latency)
+constexpr long long kGraphStates = 1ll << 22;
 // Green's function runs re-orthogonalise only sectors up to this size
 constexpr long long kGfReorthStates = 1ll << 22;
 
@@ -213,8 +216,12 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
   const bool pro = partial && !reorth && basis && basis->kind == BASIS_SAME && basis->complete;
   OmegaPRO om;
   double anorm = 0.0;
-  for (int j = 0; j < max_iter && !done; ++j) {
-    bool ortho_now = false;
+  int* hcount = nullptr;  // device index of the next history entry
+  ED_TRY(mem.get((void**)&hcount, sizeof(int)));
+  ED_CUDA_TRY(cudaMemsetAsync(hcount, 0, sizeof(int), st));
+  // one step up to its history entry (apply, alpha, beta, orthogonalisation)
+  auto head = [&](int j, bool& ortho_now) -> ed_status {
+    ortho_now = false;
     if constexpr (std::is_same<T, double>::value) {
       if (prepared)
         ED_TRY(apply_prepared_fixed(c, v, w, st));
@@ -252,45 +259,12 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
         ortho_now = true;
       }
     }
-    ED_CUDA_TRY(cudaMemcpyAsync(hist + 2 * j, slot(c, 0), 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_hist_push(c, hist, hcount, st);
     ED_CUDA_TRY(cudaGetLastError());
-    const int m = j + 1;
-    if (m % every == 0 || m == max_iter) {
-      // read the new steps' scalars and examine them in order
-      hbuf.resize((size_t)(m - read) * 2);
-      ED_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), hist + 2 * read, hbuf.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                  st));
-      ED_CUDA_TRY(cudaStreamSynchronize(st));
-      for (int k = read; k < m && !done; ++k) {
-        const double a = hbuf[2 * (k - read)], b = hbuf[2 * (k - read) + 1];
-        out.alpha.push_back(a);
-        out.beta.push_back(b);
-        scale = std::max(scale, std::fabs(a) + b);
-        const int mk = k + 1;
-        const bool breakdown = !(b > 1e-13 * (scale > 0 ? scale : 1.0));
-        if (!fixed && (mk % check_every == 0 || breakdown)) {
-          double th = tridiag_lowest(out.alpha.data(), out.beta.data(), mk);
-          bool ok = std::fabs(th - theta_prev) <= tol * std::fabs(th);
-          if (ok && resid_tol > 0.0 && !breakdown) {
-            std::vector<double> sv;
-            tridiag_vector(out.alpha.data(), out.beta.data(), mk, th, sv);
-            ok = std::fabs(b * sv[mk - 1]) <= resid_tol * std::max(1.0, std::fabs(th));
-          }
-          if (ok) {
-            out.converged = true;
-            done = true;
-          }
-          theta_prev = th;
-        }
-        if (breakdown) {
-          out.converged = true;  // invariant subspace: T is exact
-          done = true;
-        }
-      }
-      read = m;
-      if (done) break;
-    }
-    if (m == max_iter) break;
+    return ED_OK;
+  };
+  // the rest of the step: the next Lanczos vector (and its fixed-point copy)
+  auto tail = [&](bool ortho_now) {
     if constexpr (std::is_same<T, double>::value) {
       // (after an orthogonalisation the exponent lz_b recorded may be stale)
       if (fuse && c->d_fixed && !ortho_now) {
@@ -305,6 +279,118 @@ ed_status lz_run(ed_ctx* c, cudaStream_t st, T* bufs[3], const T* v0, int max_it
     }
     std::swap(vprev, v);
     basis_store<T>(c, basis, v, n, st);
+  };
+  // read the scalars of the steps since the last read and examine them in order
+  auto examine = [&](int m) -> ed_status {
+    hbuf.resize((size_t)(m - read) * 2);
+    ED_CUDA_TRY(cudaMemcpyAsync(hbuf.data(), hist + 2 * read, hbuf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                st));
+    ED_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = read; k < m && !done; ++k) {
+      const double a = hbuf[2 * (k - read)], b = hbuf[2 * (k - read) + 1];
+      out.alpha.push_back(a);
+      out.beta.push_back(b);
+      scale = std::max(scale, std::fabs(a) + b);
+      const int mk = k + 1;
+      const bool breakdown = !(b > 1e-13 * (scale > 0 ? scale : 1.0));
+      if (!fixed && (mk % check_every == 0 || breakdown)) {
+        double th = tridiag_lowest(out.alpha.data(), out.beta.data(), mk);
+        bool ok = std::fabs(th - theta_prev) <= tol * std::fabs(th);
+        if (ok && resid_tol > 0.0 && !breakdown) {
+          std::vector<double> sv;
+          tridiag_vector(out.alpha.data(), out.beta.data(), mk, th, sv);
+          ok = std::fabs(b * sv[mk - 1]) <= resid_tol * std::max(1.0, std::fabs(th));
+        }
+        if (ok) {
+          out.converged = true;
+          done = true;
+        }
+        theta_prev = th;
+      }
+      if (breakdown) {
+        out.converged = true;  // invariant subspace: T is exact
+        done = true;
+      }
+    }
+    read = m;
+    return ED_OK;
+  };
+  // small sectors: pairs of steps (the v / vprev roles alternate, so a pair
+  // returns them to where they started) captured once and replayed
+  // (captured on the context's private stream and fenced with events
+  // against the caller's stream, which may be the legacy default stream)
+  bool graphs = n <= kGraphStates && !reorth && !pro && !(basis && basis->complete) && !c->prof && max_iter > 3;
+  struct GraphState {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t fence[2] = {nullptr, nullptr};
+    void release() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      exec = nullptr;
+      graph = nullptr;
+    }
+    ~GraphState() {
+      release();
+      for (auto& e : fence)
+        if (e) cudaEventDestroy(e);
+    }
+  } gs;
+  cudaGraph_t& graph = gs.graph;
+  cudaGraphExec_t& gexec = gs.exec;
+  cudaEvent_t* fence = gs.fence;
+  if (graphs) {
+    if (!c->lz_stream && cudaStreamCreateWithFlags(&c->lz_stream, cudaStreamNonBlocking) != cudaSuccess)
+      c->lz_stream = nullptr;
+    for (int q = 0; q < 2; ++q)
+      if (cudaEventCreateWithFlags(&fence[q], cudaEventDisableTiming) != cudaSuccess) fence[q] = nullptr;
+    graphs = c->lz_stream && fence[0] && fence[1];
+    cudaGetLastError();
+  }
+  auto release = [&]() { gs.release(); };
+  int j = 0;
+  while (j < max_iter && !done) {
+    if (graphs && j >= 1 && j + 2 < max_iter) {
+      const cudaStream_t user = st, ps = c->lz_stream;
+      if (!gexec) {
+        st = ps;
+        bool ok = cudaStreamBeginCapture(ps, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        ed_status es = ED_OK;
+        if (ok) {
+          for (int q = 0; q < 2 && es == ED_OK; ++q) {
+            bool on = false;
+            es = head(j + q, on);
+            if (es == ED_OK) tail(on);
+          }
+          ok = cudaStreamEndCapture(ps, &graph) == cudaSuccess && es == ED_OK &&
+               cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+        }
+        st = user;
+        if (!ok) {
+          // nothing captured has run: continue step by step
+          cudaGetLastError();
+          release();
+          graphs = false;
+          continue;
+        }
+      }
+      ED_CUDA_TRY(cudaEventRecord(fence[0], st));
+      ED_CUDA_TRY(cudaStreamWaitEvent(ps, fence[0], 0));
+      const cudaError_t le = cudaGraphLaunch(gexec, ps);
+      if (le != cudaSuccess) {
+        release();
+        ED_CUDA_TRY(le);
+      }
+      ED_CUDA_TRY(cudaEventRecord(fence[1], ps));
+      ED_CUDA_TRY(cudaStreamWaitEvent(st, fence[1], 0));
+      j += 2;
+    } else {
+      bool on = false;
+      ED_TRY(head(j, on));
+      ++j;
+      if (j < max_iter) tail(on);
+    }
+    if (j - read >= every || j == max_iter) ED_TRY(examine(j));
   }
   // stop at the step the host examined last (later steps, if any, came
   // after a breakdown or convergence inside a read batch)

@@ -240,6 +240,7 @@ struct ed_ctx {
   size_t work_bytes = 0;
   double* d_partials = nullptr;
   double* h_pinned = nullptr;
+  cudaStream_t lz_stream = nullptr;  // private stream for captured Lanczos steps
   ~ed_ctx();
 };
 

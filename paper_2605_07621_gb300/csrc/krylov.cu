@@ -164,6 +164,15 @@ __global__ void k_axpy_basis(const TB* __restrict__ v, TO* __restrict__ x, doubl
     x[i] = from_d<TO>(to_d(x[i]) + s * to_d(v[i]));
 }
 
+// appends this step's alpha and beta to the device history at the step
+// index the device keeps (so the same launch serves every step of a graph)
+__global__ void k_hist_push(const double* __restrict__ sl, double* __restrict__ hist, int* counter) {
+  const int j = *counter;
+  hist[2 * j] = sl[0];
+  hist[2 * j + 1] = sl[1];
+  *counter = j + 1;
+}
+
 // x = sum_j s_j V_j over an FP32 basis (V_j = V + j n).  Each coefficient
 // comes as a float pair (hi, lo), s_j = hi + lo to about 48 bits; the
 // product hi * v is split exactly by an fma into its rounded value and
@@ -507,6 +516,9 @@ ed_status launch_combine_f32(ed_ctx* c, const float* V, long long n, const doubl
   k_combine_f32<<<grid_for(c, n), kRedThreads, (size_t)m * sizeof(float2), st>>>(V, n, m, d, x);
   ED_CUDA_TRY(cudaGetLastError());
   return ED_OK;
+}
+void launch_hist_push(ed_ctx* c, double* hist, int* counter, cudaStream_t st) {
+  k_hist_push<<<1, 1, 0, st>>>(slot(c, 0), hist, counter);
 }
 template <typename TI, typename TO>
 void launch_cvt(ed_ctx* c, const TI* x, TO* y, long long n, cudaStream_t st) {

@@ -51,6 +51,8 @@ template <typename TI, typename TO>
 void launch_scale_cvt(ed_ctx* c, const TI* x, TO* y, double s, long long n, cudaStream_t st);
 template <typename TB, typename TO>
 void launch_axpy_basis(ed_ctx* c, const TB* v, TO* x, double s, long long n, cudaStream_t st);
+// hist[2j], hist[2j+1] = alpha_j, beta_{j+1} from the scalar slots, j = *counter (incremented)
+void launch_hist_push(ed_ctx* c, double* hist, int* counter, cudaStream_t st);
 template <typename TI, typename TO>
 void launch_cvt(ed_ctx* c, const TI* x, TO* y, long long n, cudaStream_t st);
 // x = sum_j s_j V_j over m <= kMaxBasis FP32 vectors V_j = V + j n (float-float sums)

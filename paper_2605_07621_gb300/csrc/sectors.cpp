@@ -97,6 +97,7 @@ using namespace edk;
 ed_ctx::~ed_ctx() {
   for (void* p : dev_allocs) cudaFree(p);
   if (h_pinned) cudaFreeHost(h_pinned);
+  if (lz_stream) cudaStreamDestroy(lz_stream);
 }
 
 extern "C" const char* ed_last_error(void) { return edk::g_err; }

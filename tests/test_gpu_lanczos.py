@@ -235,3 +235,23 @@ def test_green_function_plain_recurrence_and_modes(ed):
     st = L.load().ed_lanczos_gf(ctx.handle, ctypes.c_void_p(psi.data_ptr()), r.e0, 0, 0, 10, omega.ctypes.data,
                                 len(omega), 0.05, Gr.ctypes.data, None, None, None, None, None, None, 7, None)
     assert st == L.ED_EINVAL
+
+
+@pytest.mark.parametrize("name,mode", [("heis16", "f64"), ("hub12", "f64"), ("hub12", "f32"),
+                                       ("qim_small", "f64")])
+def test_captured_steps_match_step_by_step(ed, name, mode):
+    """Small sectors replay pairs of Lanczos steps from a captured CUDA graph;
+    with profiling on the same run goes step by step.  Both must produce the
+    same coefficients bit for bit (same kernels, same order)."""
+    m = {"heis16": W.config_heis16(), "hub12": W.config_hub12(),
+         "qim_small": W.anderson_impurity(8, 4.0, -2.0, 0.5, W.impurity_bath(8, seed=21), 4, 5)}[name]
+    ctx = _ctx(ed, m)
+    runs = []
+    for prof in (False, True):
+        ctx.profile(prof)
+        r = ed.lanczos_ground(ctx, mode=mode, max_iter=61, fixed_iter=True)
+        runs.append(r)
+    ctx.profile(False)
+    assert runs[0].iterations == runs[1].iterations == 61
+    assert np.array_equal(runs[0].alpha, runs[1].alpha) and np.array_equal(runs[0].beta, runs[1].beta)
+    assert runs[0].e0 == runs[1].e0
