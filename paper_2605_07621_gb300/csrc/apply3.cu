@@ -59,7 +59,8 @@ constexpr bool kListsF32 = false;
 //    (padding points at a zero slot);
 //  * cross terms: one B-side map load per B cross site, shared by the R
 //    rows, then one gather per valid bond from the neighbouring block (8-byte
-//    types: from per-row lists of the valid bonds for each column bit);
+//    types: from per-row lists of the valid bonds for each column bit and
+//    value class, summed per class and weighted once per column);
 //  * the diagonal from per-row constants and popcounts of packed words.
 template <class Pol, int R, int NT = kRowThreads, int MINB = 2>
 __global__ void __launch_bounds__(NT, MINB)
@@ -70,14 +71,14 @@ __global__ void __launch_bounds__(NT, MINB)
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem5);
   S* bufs = reinterpret_cast<S*>(smem5 + 128);
   __shared__ const S* src_row[R][32];  // per row, per A cross site
-  // per row, B cross site and value beta of the column's bit at that site:
-  // the site's bonds that are valid there (their A bit differs from beta),
-  // as (source row, weight) lists of at most kXL entries
-  constexpr int kXL = 4;
-  __shared__ const S* xl_ptr[R][32][2][kXL];
-  __shared__ S xl_w[R][32][2][kXL];
-  __shared__ unsigned char xl_n[R][32][2];
-  __shared__ int xl_mx[32];  // per B cross site: longest list over rows and beta
+  // per row, B cross site, value beta of the column's bit at that site and
+  // value class (of at most two): the site's bonds that are valid there
+  // (their A bit differs from beta), as source-row lists of at most kXL
+  // entries; a column sums each class's gathers and multiplies once
+  constexpr int kXL = 2;
+  __shared__ const S* xl_ptr[R][32][2][2][kXL];
+  __shared__ unsigned char xl_n[R][32][2][2];
+  __shared__ int xl_mx[32][2];  // per B cross site and class: longest list over rows and beta
   constexpr bool kLists = sizeof(S) == 8 || kListsF32;
   __shared__ int s_pad[R];
   constexpr int V = 16 / (int)sizeof(S);
@@ -157,11 +158,11 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     if (kLists && p.ncross && t.xl_ok) {
       __syncthreads();  // src_row complete
-      if (threadIdx.x < 32) xl_mx[threadIdx.x] = 0;
+      if (threadIdx.x < 64) xl_mx[threadIdx.x >> 1][threadIdx.x & 1] = 0;
       __syncthreads();
       if (threadIdx.x < R * 64) {
         const int r = threadIdx.x >> 6, ib = (threadIdx.x >> 1) & 31, beta = threadIdx.x & 1;
-        int n = 0;
+        int n0 = 0, n1 = 0;
         if (ib < t.n_ib && r < nr) {
           const unsigned par = t.A_pack[bl.gA0 + a0 + r];
           unsigned km = t.ib_mask[ib];
@@ -169,15 +170,19 @@ __global__ void __launch_bounds__(NT, MINB)
             const int k = __ffs(km) - 1;
             km &= km - 1;
             const S* sp = src_row[r][t.bond_ia[k]];
-            if ((((par >> k) & 1u) != (unsigned)beta) && sp) {  // at most kXL (xl_ok)
-              xl_ptr[r][ib][beta][n] = sp;
-              xl_w[r][ib][beta][n] = Pol::bw(t, k);
-              ++n;
+            if ((((par >> k) & 1u) != (unsigned)beta) && sp) {  // at most kXL per class (xl_ok)
+              if ((t.xl_c1_mask >> k) & 1u) {
+                if (n1 < kXL) xl_ptr[r][ib][beta][1][n1++] = sp;
+              } else {
+                if (n0 < kXL) xl_ptr[r][ib][beta][0][n0++] = sp;
+              }
             }
           }
         }
-        xl_n[r][ib][beta] = (unsigned char)n;
-        atomicMax(&xl_mx[ib], n);
+        xl_n[r][ib][beta][0] = (unsigned char)n0;
+        xl_n[r][ib][beta][1] = (unsigned char)n1;
+        atomicMax(&xl_mx[ib][0], n0);
+        atomicMax(&xl_mx[ib][1], n1);
       }
     }
     const bool ok = bar_wait(&bar[0], phase);
@@ -246,33 +251,48 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
         for (int r = 0; r < R; ++r) dr[r] = r < nr ? (pa[r] ^ pb) : 0u;
         if (kLists && t.xl_ok) {
-          // per B cross site, the column's bit there picks each row's list of
-          // valid bonds; the gathers of all rows' lists are issued before any
-          // is summed, and the next site's map entry is loaded one site ahead
+          // per B cross site, the column's bit there picks each row's lists of
+          // valid bonds (one per value class); the gathers of all rows' lists are
+          // issued before any is summed (invalid slots read nothing and add zero),
+          // the next site's map entry is loaded one site ahead, and each class's
+          // sum is multiplied by its weight once per column
           unsigned mq_next = t.n_ib > 0 ? __ldg(t.mapB + gB) : 0u;
+          S s0[R], s1[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) s0[r] = s1[r] = 0;
           for (int ib = 0; ib < t.n_ib; ++ib) {
             const unsigned mq = mq_next;
             if (ib + 1 < t.n_ib) mq_next = __ldg(t.mapB + (long long)(ib + 1) * t.B_total + gB);
-            const int mx = xl_mx[ib];
-            if (!mx) continue;
+            const int mx0 = xl_mx[ib][0], mx1 = xl_mx[ib][1];
+            if (!(mx0 | mx1)) continue;
             const int beta = (int)((pb >> (__ffs(t.ib_mask[ib]) - 1)) & 1u);
-            int nn[R];
-            S v[R][kXL];
+            int n0[R], n1[R];
+            S v0[R][kXL], v1[R][kXL];
 #pragma unroll
-            for (int r = 0; r < R; ++r) nn[r] = xl_n[r][ib][beta];
+            for (int r = 0; r < R; ++r) {
+              n0[r] = xl_n[r][ib][beta][0];
+              n1[r] = xl_n[r][ib][beta][1];
+            }
+#pragma unroll
+            for (int i = 0; i < kXL; ++i) {
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                v0[r][i] = (i < mx0 && i < n0[r]) ? __ldg(xl_ptr[r][ib][beta][0][i] + mq) : (S)0;
+                v1[r][i] = (i < mx1 && i < n1[r]) ? __ldg(xl_ptr[r][ib][beta][1][i] + mq) : (S)0;
+              }
+            }
 #pragma unroll
             for (int i = 0; i < kXL; ++i)
-              if (i < mx) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[r][i] = i < nn[r] ? __ldg(xl_ptr[r][ib][beta][i] + mq) : (S)0;
+              for (int r = 0; r < R; ++r) {
+                s0[r] += v0[r][i];
+                s1[r] += v1[r][i];
               }
+          }
+          {
+            const S w0 = Pol::w(t, t.xl_c[0]), w1 = Pol::w(t, t.xl_c[1]);
 #pragma unroll
-            for (int i = 0; i < kXL; ++i)
-              if (i < mx) {
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                  if (i < nn[r]) acc[r] += xl_w[r][ib][beta][i] * v[r][i];
-              }
+            for (int r = 0; r < R; ++r) acc[r] += w0 * s0[r] + w1 * s1[r];
           }
         } else if constexpr (sizeof(S) == 4) {
           // 4-byte types (four rows per pass): loop over every bond with

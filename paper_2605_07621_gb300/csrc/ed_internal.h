@@ -154,7 +154,10 @@ struct Dev3 {
   // cross bonds grouped by B site: bonds with B site ib are bits ib_mask[ib]
   int n_ib;
   int n_ia;
-  int xl_ok;                // every B cross site has at most 4 bonds (row-pass bond lists)
+  int xl_ok;                // row-pass bond lists apply: the cross bonds take at most two
+                            // value classes, each B cross site at most two bonds of each
+  int xl_c[2];              // the two classes (equal when there is one)
+  unsigned xl_c1_mask;      // cross bonds (bit k) of class xl_c[1] (the rest are xl_c[0])
   unsigned ib_mask[32];
   unsigned ia_mask[32];     // bonds (bits) whose A site is ia
   unsigned char bond_ib[32];

@@ -212,9 +212,20 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   }
   t.n_ib = (int)c->crossB_bits.size();
   t.n_ia = (int)c->crossA_bits.size();
-  t.xl_ok = 1;
-  for (int ib = 0; ib < t.n_ib; ++ib)
-    if (__builtin_popcount(t.ib_mask[ib]) > 4) t.xl_ok = 0;
+  // bond lists of the row pass: per B cross site and value class at most two
+  // bonds, at most two classes over all cross bonds
+  {
+    std::vector<int> cc;
+    for (int ci : c->cross_cls)
+      if (std::find(cc.begin(), cc.end(), ci) == cc.end()) cc.push_back(ci);
+    t.xl_ok = cc.size() <= 2 ? 1 : 0;
+    t.xl_c[0] = cc.empty() ? 0 : cc[0];
+    t.xl_c[1] = cc.size() > 1 ? cc[1] : t.xl_c[0];
+    t.xl_c1_mask = cc.size() > 1 ? t.cross_cls_mask[cc[1]] : 0u;
+    for (int ib = 0; t.xl_ok && ib < t.n_ib; ++ib)
+      if (__builtin_popcount(t.ib_mask[ib] & ~t.xl_c1_mask) > 2 || __builtin_popcount(t.ib_mask[ib] & t.xl_c1_mask) > 2)
+        t.xl_ok = 0;
+  }
   const DevDiagParams& dp = c->diag;
   t.vab_and = dp.vab_and;
   t.ncls_d = dp.ncls;
