@@ -199,8 +199,8 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
                         const double* omega, int n_omega, double eta, double* G, double* a_p, double* b_p,
                         double* a_h, double* b_h, double* w_p, double* w_h, int reorth, void* stream);
 
-/* Entanglement spectrum of a state across the cut (paper Sec. 3, figure
- * "Distributed entanglement spectrum"): the eigenvalues lambda of the
+/* Entanglement spectrum of a state across the cut (the paper's discussion
+ * of its figure "Distributed entanglement spectrum"): the eigenvalues lambda of the
  * reduced density matrix rho_A = Tr_B |psi><psi|, whose logarithms give the
  * spectrum xi = -log(lambda) of the entanglement Hamiltonian, resolved by the
  * charge s of side A, with the sector weights W_s = sum_i lambda_{s,i} /

@@ -383,7 +383,7 @@ def entanglement_spectrum(model, keys: np.ndarray, psi: np.ndarray):
     """Entanglement spectrum of psi across the model's cut.
 
     The paper's entanglement Hamiltonian is H_E = -log rho_L with
-    rho_L = Tr_R |psi><psi| (its Sec. 3 and the figure on the distributed
+    rho_L = Tr_R |psi><psi| (its discussion of the figure on the distributed
     entanglement spectrum), with spectrum xi_{q,i} per charge q of the left
     side and sector weights W_q = sum_i exp(-xi_{q,i}) / sum_{q,i} exp(-xi_{q,i}).
     Written out: rho_A is block diagonal in the charge s of side A, and the

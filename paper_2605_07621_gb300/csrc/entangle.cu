@@ -1,7 +1,7 @@
 // Entanglement spectrum across the cut: the spectrum xi = -log(lambda) of
 // the entanglement Hamiltonian H_E = -log(rho_A), rho_A = Tr_B |psi><psi|,
-// resolved by the conserved charge of side A (paper Sec. 3, figure
-// "Distributed entanglement spectrum", with the sector weights W_q).
+// resolved by the conserved charge of side A (the paper's discussion of
+// its figure "Distributed entanglement spectrum", with the sector weights W_q).
 //
 // In the block layout rho_A is block diagonal, rho_A(s) = Psi_s Psi_s^T, and
 // its nonzero eigenvalues are those of the Gram matrix of Psi_s in the
