@@ -255,3 +255,20 @@ def test_captured_steps_match_step_by_step(ed, name, mode):
     assert runs[0].iterations == runs[1].iterations == 61
     assert np.array_equal(runs[0].alpha, runs[1].alpha) and np.array_equal(runs[0].beta, runs[1].beta)
     assert runs[0].e0 == runs[1].e0
+
+
+def test_captured_steps_on_a_user_stream(ed):
+    """The captured steps run on the context's private stream, fenced against
+    the caller's stream: on a user stream (and with work queued on it before
+    the call) the coefficients equal those of the default-stream run."""
+    import torch
+
+    ctx = _ctx(ed, W.config_hub12())
+    r0 = ed.lanczos_ground(ctx, mode="f64", max_iter=61, fixed_iter=True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        junk = torch.randn(1 << 22, device="cuda")
+        junk.mul_(2.0)  # queued ahead of the Lanczos run on the same stream
+        r1 = ed.lanczos_ground(ctx, mode="f64", max_iter=61, fixed_iter=True, stream=s)
+    s.synchronize()
+    assert np.array_equal(r0.alpha, r1.alpha) and np.array_equal(r0.beta, r1.beta)
