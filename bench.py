@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
     p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
     p.add_argument("--no-entangle", action="store_true", help="skip the entanglement spectrum of the ground state")
+    p.add_argument("--no-dense", action="store_true", help="skip the dense-block (DMRG-style) H psi")
     p.add_argument("--row-pass", default="auto", choices=["auto", "single", "staged", "push"],
                    help="pin the row pass of the headline workload (default: the library's choice)")
     return p.parse_args()
@@ -132,6 +133,50 @@ def entanglement_section(ed, ctx):
             "entropy": es.entropy, "s": [int(v) for v in s], "W_q": [float(v) for v in W],
             "xi_lowest_per_sector": xi_low, "n_eff_weights": float(1.0 / np.sum(W ** 2)),
             "n_eff_dims": float(1.0 / np.sum(w_dim ** 2)), "levels": int(sum(len(l) for l in es.lam))}
+
+
+def dense_blocks_section(ed):
+    """Dense-block H|psi> (DMRG-style side operators) on the paper's block-size
+    laws chi_q = C e^{-alpha |q - q0|}, sum chi about 4000, 21 sectors, two
+    adjoint pairs of cross terms: device time per apply (CUDA events) and the
+    FP64 FLOP rate against the FP64 peak (parity is checked by the tests)."""
+    import torch
+
+    import workloads.dense as WD
+
+    out = {}
+    for alpha in (0.95, 0.15, 1.11):
+        m = WD.dense_config(alpha)
+        op = ed.DenseOperator(m)
+        flops = 0.0
+        for c in m.chi.astype(np.float64):
+            flops += 4.0 * c ** 3
+        for d, Ls in zip(m.delta, m.Lm):
+            for q, l in enumerate(Ls):
+                if l is not None:
+                    ct, c = l.shape
+                    flops += 2.0 * ct * c * c + 2.0 * ct * ct * c
+        rng = np.random.default_rng(3)
+        x = rng.standard_normal(m.dim)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty_like(xd)
+        for _ in range(2):
+            op.apply(xd, yd)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            op.apply(xd, yd)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        tf = flops / (ms * 1e-3) / 1e12
+        out[f"alpha_{alpha}"] = {"chi_max": int(m.chi.max()), "sum_chi": int(m.chi.sum()), "states": m.dim,
+                                 "ms": ms, "tflops": tf, "frac_fp64_peak": tf / FP64_TFLOPS_NOMINAL,
+                                 "flops": flops}
+        op.close()
+        del xd, yd
+    return out
 
 
 def kernel_source_hash():
@@ -572,6 +617,14 @@ def main():
         except Exception as exc:
             entangle = {"error": str(exc)}
 
+    dense = None
+    if not args.no_dense and rank == 0:
+        torch.cuda.empty_cache()
+        try:
+            dense = dense_blocks_section(ed)
+        except Exception as exc:
+            dense = {"error": str(exc)}
+
     batched = served = None
     if not args.no_batched:
         torch.cuda.empty_cache()
@@ -611,7 +664,8 @@ def main():
                            "setup_s": t_setup, "row_pass": ctx.row_pass(tdt)},
                 "gpu_launches": args.steps * (4 if args.dtype == "f64" else 2),
                 "roofline": roof, "clocks": clk, "e2e": e2e, "other_precision": other, "lanczos": lanczos,
-                "entanglement": entangle, "batched": batched, "serving": served, "configs": configs,
+                "entanglement": entangle, "dense_blocks": dense, "batched": batched, "serving": served,
+                "configs": configs,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -226,6 +226,29 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
                                    double* weight, double* entropy, double* stage_ms, void* stream);
 
+/* ---- dense-block form -----------------------------------------------------
+ * The bipartite operator of paper Eq. (2) with dense side operators on
+ * symmetry blocks (its DMRG setting): blocks q = 0..nq-1 of dimension
+ * chi[q] x chi[q] (left x right index), the state the concatenation of the
+ * row-major blocks Psi_q (dimension sum_q chi_q^2), and
+ *   (H psi)_q' = H_L,q' Psi_q' + Psi_q' H_R,q'^T + sum_m L_m,q Psi_q R_m,q^T
+ * over the cross terms m with q' = q + delta[m] (the Vec identity
+ * [L (x) R] Vec(Psi) = Vec(L Psi R^T), row-major).  Every product runs in
+ * this library's FP64 batched GEMM kernel, one launch per stage.
+ *   HL, HR   host pointers, one per block: chi_q x chi_q row-major
+ *   delta    per cross term, nonzero
+ *   Lm, Rm   host pointers [m * nq + q]: chi_{q+delta} x chi_q row-major for
+ *            the source blocks q with q + delta inside 0..nq-1, NULL otherwise
+ * The matrices are copied to the device; the caller keeps its own.
+ * ed_dense_apply: x, y device FP64 vectors of ed_dense_dim elements, not
+ * overlapping; asynchronous on the stream. */
+typedef struct ed_dense ed_dense;
+ed_status ed_dense_create(int nq, const int64_t* chi, const double* const* HL, const double* const* HR, int n_terms,
+                          const int* delta, const double* const* Lm, const double* const* Rm, ed_dense** out);
+int64_t ed_dense_dim(const ed_dense* d);
+ed_status ed_dense_apply(ed_dense* d, const double* x, double* y, void* stream);
+void ed_dense_destroy(ed_dense* d);
+
 /* ---- batched form -------------------------------------------------------
  * Many independent single-block instances (Hubbard models with the spin
  * cut) packed into one device arena and stepped together: every kernel is

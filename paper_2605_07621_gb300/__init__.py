@@ -21,6 +21,7 @@ from .ed import (  # noqa: E402,F401
     batch_create,
     batch_lanczos,
     Context,
+    DenseOperator,
     LanczosResult,
     Server,
     apply_H,
@@ -35,7 +36,7 @@ from .ed import (  # noqa: E402,F401
 )
 from ._lib import EDError  # noqa: E402,F401
 
-__all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "LanczosResult", "Server", "apply_H", "apply_H_noalloc", "build_local_ops", "build_sectors",
+__all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "DenseOperator", "LanczosResult", "Server", "apply_H", "apply_H_noalloc", "build_local_ops", "build_sectors",
            "EntanglementSpectrum", "entanglement_spectrum", "lanczos_gf",
            "lanczos_ground", "random_vector", "EDError", "OPS_DEFAULT", "OPS_FORCE_CSR", "OPS_FORCE_DENSE",
            "OPS_ROW_SINGLE", "OPS_ROW_STAGED", "OPS_ROW_PUSH"]

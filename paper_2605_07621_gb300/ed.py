@@ -305,6 +305,63 @@ def entanglement_spectrum(ctx: Context, psi, stream=None) -> EntanglementSpectru
     return EntanglementSpectrum(s, np.split(lam[: n.value], cuts), wt, ent.value, (float(ms[0]), float(ms[1])))
 
 
+class DenseOperator:
+    """Owns an ``ed_dense*``: the bipartite operator with dense side operators
+    on symmetry blocks (``ed_dense_create``), built from a
+    ``workloads.dense.DenseBlocks``."""
+
+    def __init__(self, blocks):
+        nq = len(blocks.chi)
+        keep = []
+
+        def arr(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data
+
+        chi = np.ascontiguousarray(blocks.chi, dtype=np.int64)
+        HL = (ctypes.c_void_p * nq)(*[arr(h) for h in blocks.HL])
+        HR = (ctypes.c_void_p * nq)(*[arr(h) for h in blocks.HR])
+        nt = len(blocks.delta)
+        delta = np.ascontiguousarray(blocks.delta, dtype=np.int32)
+        Lm = (ctypes.c_void_p * max(nt * nq, 1))()
+        Rm = (ctypes.c_void_p * max(nt * nq, 1))()
+        for m in range(nt):
+            for q in range(nq):
+                if blocks.Lm[m][q] is not None:
+                    Lm[m * nq + q] = arr(blocks.Lm[m][q])
+                    Rm[m * nq + q] = arr(blocks.Rm[m][q])
+        h = ctypes.c_void_p()
+        L.check(L.load().ed_dense_create(nq, chi.ctypes.data, HL, HR, nt, delta.ctypes.data if nt else None, Lm, Rm,
+                                         ctypes.byref(h)))
+        self._h = h
+        self.blocks = blocks
+
+    @property
+    def dim(self) -> int:
+        return int(L.load().ed_dense_dim(self._h))
+
+    def apply(self, x, y, stream=None):
+        import torch
+
+        for v, nm in ((x, "x"), (y, "y")):
+            if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64 and v.is_contiguous()
+                    and v.numel() == self.dim):
+                raise ValueError(f"{nm} must be a contiguous CUDA float64 tensor of {self.dim} elements")
+        L.check(L.load().ed_dense_apply(self._h, _ptr(x), _ptr(y), _stream_handle(stream)))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            L.load().ed_dense_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Owns an ``ed_batch*`` (batched independent instances)."""
 

@@ -128,3 +128,22 @@ def test_malformed_models_rejected(edlib):
     mask_out = W.heisenberg_chain(6, cut_mask=1 << 7)
     with pytest.raises(EDError, match="ED_EINVAL"):
         edlib.build_sectors(mask_out)
+
+
+def test_dense_create_rejects_bad_arguments(edlib):
+    """Argument checks of ed_dense_create run before any device call."""
+    import ctypes
+
+    from paper_2605_07621_gb300 import _lib as L
+
+    lib = L.load()
+    chi = np.array([2, 3], dtype=np.int64)
+    h = [np.eye(2), np.eye(3)]
+    HL = (ctypes.c_void_p * 2)(*[a.ctypes.data for a in h])
+    delta = np.array([0], dtype=np.int32)  # a cross term must move the charge
+    Lm = (ctypes.c_void_p * 2)()
+    out = ctypes.c_void_p()
+    assert lib.ed_dense_create(2, chi.ctypes.data, HL, HL, 1, delta.ctypes.data, Lm, Lm, ctypes.byref(out)) == L.ED_EINVAL
+    bad = np.array([2, 0], dtype=np.int64)  # empty block
+    assert lib.ed_dense_create(2, bad.ctypes.data, HL, HL, 0, None, None, None, ctypes.byref(out)) == L.ED_EINVAL
+    assert not out.value
