@@ -15,6 +15,7 @@ from .ed import (  # noqa: F401
     sector_dim,
     apply_H,
     apply_H_rows,
+    RowIndex,
     dense_H,
     row_terms,
     find_keys,

@@ -98,6 +98,13 @@ def _get():
                                       ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_void_p]
         lib.or_num_threads.restype = ctypes.c_int
+        lib.or_index_new.restype = ctypes.c_void_p
+        lib.or_index_new.argtypes = [P(_OrModel), ctypes.c_void_p, ctypes.c_int64]
+        lib.or_index_delete.restype = None
+        lib.or_index_delete.argtypes = [ctypes.c_void_p]
+        lib.or_apply_rows_ix.restype = ctypes.c_int
+        lib.or_apply_rows_ix.argtypes = [P(_OrModel), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -175,6 +182,39 @@ def apply_H_rows(model, keys: np.ndarray, x: np.ndarray, r0: int, r1: int, nthre
     return y[: r1 - r0]
 
 
+class RowIndex:
+    """The lookup index of one sector's sorted keys, built once, for repeated
+    evaluations of listed rows of y = H x (same arithmetic per row as
+    ``apply_H``).  Keeps references to the keys and the model."""
+
+    def __init__(self, model, keys: np.ndarray):
+        self.keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        self.ref = _ModelRef(model)
+        self.h = _get().or_index_new(self.ref.ptr, self.keys.ctypes.data, len(self.keys))
+        if not self.h:
+            raise MemoryError("oracle: index allocation failed")
+
+    def apply_rows(self, x: np.ndarray, rows: np.ndarray, nthreads: int = 0) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        y = np.empty(max(len(rows), 1), dtype=np.float64)
+        if _get().or_apply_rows_ix(self.ref.ptr, self.h, x.ctypes.data, rows.ctypes.data, len(rows), y.ctypes.data,
+                                   int(nthreads)) != 0:
+            raise RuntimeError("oracle: H connects a state outside the sector basis (or a row is out of range)")
+        return y[: len(rows)]
+
+    def close(self):
+        if self.h:
+            _get().or_index_delete(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dense_H(model, keys: np.ndarray) -> np.ndarray:
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     D = len(keys)
@@ -238,7 +278,12 @@ def lanczos(matvec, v0: np.ndarray, n_iter: int, reorth: bool = True, keep_basis
     nrm = np.linalg.norm(v)
     v /= nrm
     alphas, betas = [], []
-    basis = [v] if (reorth or keep_basis) else None
+    # the Krylov vectors, row k = v_k (rows 0..k-1 are the basis so far)
+    basis = np.empty((n_iter + 1, len(v))) if (reorth or keep_basis) else None
+    nb = 0
+    if basis is not None:
+        basis[0] = v
+        nb = 1
     v_prev = np.zeros_like(v)
     beta = 0.0
     for j in range(n_iter):
@@ -248,7 +293,7 @@ def lanczos(matvec, v0: np.ndarray, n_iter: int, reorth: bool = True, keep_basis
         if j > 0:
             w -= beta * v_prev
         if reorth:
-            B = np.array(basis)
+            B = basis[:nb]
             for _ in range(2):
                 w -= B.T @ (B @ w)
         b = float(np.linalg.norm(w))
@@ -259,10 +304,12 @@ def lanczos(matvec, v0: np.ndarray, n_iter: int, reorth: bool = True, keep_basis
         v_prev, v = v, w / b
         beta = b
         if basis is not None:
-            basis.append(v)
+            basis[nb] = v
+            v = basis[nb]
+            nb += 1
     V = None
     if keep_basis:
-        V = np.array(basis[: len(alphas)])
+        V = basis[: len(alphas)].copy()
     return np.array(alphas), np.array(betas), V
 
 

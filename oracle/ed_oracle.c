@@ -170,6 +170,7 @@ static void index_build(or_index* ix, const or_model* m, const uint64_t* keys, i
   ix->shift = nbits - bb;
   ix->nb = (int64_t)1 << bb;
   ix->bucket = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ix->nb + 1));
+  if (!ix->bucket) return;
   int64_t p = 0;
   for (int64_t h = 0; h < ix->nb; ++h) {
     while (p < D && (keys[p] >> ix->shift) < (uint64_t)h) ++p;
@@ -206,6 +207,23 @@ int or_find(const or_model* m, const uint64_t* keys, int64_t D, const uint64_t* 
 
 #define ROW_CAP 512
 
+/* (H x)[r] for one row r of the sorted basis: the diagonal term plus every
+ * off-diagonal term, in the order or_row lists them.  Sets *bad if a
+ * connected state is missing from the basis. */
+static double row_value(const or_model* m, const or_index* ix, const uint64_t* keys, const double* x, int64_t r,
+                        uint64_t* nk, double* nv, int* bad) {
+  double diag;
+  int c = or_row(m, keys[r], &diag, nk, nv, ROW_CAP);
+  if (c < 0) { *bad = 1; return 0.0; }
+  double acc = diag * x[r];
+  for (int e = 0; e < c; ++e) {
+    int64_t col = index_find(ix, nk[e]);
+    if (col < 0) { *bad = 1; continue; }
+    acc += nv[e] * x[col];
+  }
+  return acc;
+}
+
 /* Rows [r0, r1) of y = H x on the full sector with sorted basis `keys`
  * (length D); y has r1 - r0 entries.  Returns 0, or -1 if a connected state
  * is missing from the basis (which would mean H leaves the sector). */
@@ -224,20 +242,50 @@ int or_apply_range(const or_model* m, const uint64_t* keys, int64_t D, const dou
     uint64_t nk[ROW_CAP];
     double nv[ROW_CAP];
 #pragma omp for schedule(static)
-    for (int64_t r = r0; r < r1; ++r) {
-      double diag;
-      int c = or_row(m, keys[r], &diag, nk, nv, ROW_CAP);
-      if (c < 0) { bad = 1; continue; }
-      double acc = diag * x[r];
-      for (int e = 0; e < c; ++e) {
-        int64_t col = index_find(&ix, nk[e]);
-        if (col < 0) { bad = 1; continue; }
-        acc += nv[e] * x[col];
-      }
-      y[r - r0] = acc;
-    }
+    for (int64_t r = r0; r < r1; ++r) y[r - r0] = row_value(m, &ix, keys, x, r, nk, nv, &bad);
   }
   index_free(&ix);
+  return bad ? -1 : 0;
+}
+
+/* A lookup index built once and kept (for repeated row evaluations of one
+ * large sector): or_index_new returns NULL on allocation failure. */
+void* or_index_new(const or_model* m, const uint64_t* keys, int64_t D) {
+  or_index* ix = (or_index*)malloc(sizeof(or_index));
+  if (!ix) return NULL;
+  index_build(ix, m, keys, D);
+  if (!ix->bucket) { free(ix); return NULL; }
+  return ix;
+}
+
+void or_index_delete(void* h) {
+  if (!h) return;
+  index_free((or_index*)h);
+  free(h);
+}
+
+/* y[i] = (H x)[rows[i]] for n listed rows, with an index from or_index_new
+ * over the same sorted keys; same arithmetic per row as or_apply_range. */
+int or_apply_rows_ix(const or_model* m, const void* h, const double* x, const int64_t* rows, int64_t n, double* y,
+                     int nthreads) {
+  const or_index* ix = (const or_index*)h;
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel reduction(| : bad)
+  {
+    uint64_t nk[ROW_CAP];
+    double nv[ROW_CAP];
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t r = rows[i];
+      if (r < 0 || r >= ix->D) { bad = 1; y[i] = 0.0; continue; }
+      y[i] = row_value(m, ix, ix->keys, x, r, nk, nv, &bad);
+    }
+  }
   return bad ? -1 : 0;
 }
 
