@@ -14,17 +14,22 @@
  * Vector layout (every x, y, psi pointer below): blocks concatenated in
  * ascending s; block s is row-major d_A(s) x d_B(s) (B index contiguous),
  * starting at element offset off[s] (ed_blocks).  Rows are the side-A
- * states of charge s in ascending bit-string order (combinadic / colex
- * rank), columns the side-B states likewise.  Bit p of a side-A string is
- * the p-th site of the A side in ascending site order (Hubbard spin cut:
- * side A = spin-up occupations, side B = spin-down occupations).
+ * states of charge s in ascending order of their side-local bit strings
+ * (combinadic / colex rank), columns the side-B states likewise.  Which
+ * lattice site each side-local bit stands for is reported by ed_side_sites:
+ * for spin models side A lists its sites on a cross-cut bond first, side B
+ * lists them last, each group in ascending site order; for the Hubbard spin
+ * cut bit p is site p on both sides (side A = spin-up occupations, side B =
+ * spin-down occupations).
  *
  * Ownership: the caller owns every vector it passes (device pointers unless
  * stated); the context owns all operator tables, maps and work buffers.
  * Errors: every call returns an ed_status and never aborts; ed_last_error()
  * gives a message for the calling thread.  Streams: the caller's stream is
  * used; no call synchronises the device except where it returns host
- * scalars (noted per call).
+ * scalars (noted per call).  Devices: a context lives on the device that
+ * was current when it was built; every call runs there and puts the calling
+ * thread's current device back before it returns.
  */
 #ifndef ED_H
 #define ED_H
@@ -86,21 +91,10 @@ ed_status ed_build_sectors(const ed_model_desc* model, ed_ctx** out);
 /* Build the side operators of Eq. (2) on the device: CSR of H_A,s and
  * H_B,s off-diagonals, side diagonals, the cross-cut maps.
  * flags: ED_OPS_DEFAULT, or ED_OPS_FORCE_CSR / ED_OPS_FORCE_DENSE to pin the
- * per-sector choice instead of autotuning it; optionally or-ed with one of
- * one of ED_OPS_ROW_SINGLE / ED_OPS_ROW_STAGED / ED_OPS_ROW_PUSH to pick how
- * spin models with cross-cut bonds get their cross terms (single, the
- * default: gathered from x in global memory by the row pass; staged: each
- * output row stages its source rows in shared memory, one CTA per SM;
- * push: each source row, staged once, is added into its target rows with
- * atomic adds).  The results are identical up to FP summation order
- * (bit-identical in the exact fixed-point FP64 mode; push makes the FP32
- * summation order run-dependent).  Synchronises the device. */
+ * per-sector choice instead of autotuning it.  Synchronises the device. */
 #define ED_OPS_DEFAULT 0
 #define ED_OPS_FORCE_CSR 1
 #define ED_OPS_FORCE_DENSE 2
-#define ED_OPS_ROW_SINGLE 4
-#define ED_OPS_ROW_STAGED 8
-#define ED_OPS_ROW_PUSH 16
 ed_status ed_build_local_ops(ed_ctx* ctx, int flags);
 
 /* y = H x over the whole sector (all blocks), device pointers of ed_dim
@@ -119,14 +113,17 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* x, void* y, ed_dtype dtype, void* 
  * for such callers.  The exact fixed-point path needs a scratch copy of x
  * (8 bytes per state); here that scratch is a fixed device array compiled
  * into the library (32 MiB, held by every GPU that loads the library until
- * the process exits), so sectors above 4,194,272 states are rejected with
- * ED_EINVAL.  Models whose couplings are not dyadic use the FP64 kernels,
- * which need no scratch.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents: two calls
- * that overlap on the GPU (different streams, or different contexts)
- * race and give wrong results.  x, y: device FP64, not overlapping,
- * x 16-byte aligned; enqueued on `stream`. */
+ * the process exits), so a context whose dimension (ed_dim: all blocks
+ * together) exceeds 4,194,272 states is rejected with ED_EINVAL.  Models
+ * whose couplings are not dyadic use the FP64 kernels, which need no
+ * scratch.  The first call on a device looks up the array's device address
+ * and keeps it for the life of the process; make that first call before
+ * any stream capture, and do not reset the device (cudaDeviceReset) between
+ * calls: the kept address would then be stale.  All calls share the array
+ * and it keeps the last call's contents: two calls that overlap on the GPU
+ * (different streams, or different contexts) race and give wrong results.
+ * x, y: device FP64, not overlapping, x 16-byte aligned; enqueued on
+ * `stream`. */
 ed_status ed_apply_H_noalloc(ed_ctx* ctx, const void* x, void* y, void* stream);
 
 /* Lanczos options / report (paper: H|psi> as the kernel of a Krylov
@@ -241,7 +238,9 @@ ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambd
  *            the source blocks q with q + delta inside 0..nq-1, NULL otherwise
  * The matrices are copied to the device; the caller keeps its own.
  * ed_dense_apply: x, y device FP64 vectors of ed_dense_dim elements, not
- * overlapping; asynchronous on the stream. */
+ * overlapping; asynchronous on the stream.  One operator holds one scratch
+ * buffer for its partial products: applies of the same operator must not
+ * overlap on the GPU (use one stream, or synchronise between them). */
 typedef struct ed_dense ed_dense;
 ed_status ed_dense_create(int nq, const int64_t* chi, const double* const* HL, const double* const* HR, int n_terms,
                           const int* delta, const double* const* Lm, const double* const* Rm, ed_dense** out);
@@ -334,9 +333,7 @@ ed_status ed_profile_enable(ed_ctx* ctx, int enable);
 ed_status ed_profile_read(ed_ctx* ctx, double* ms, int64_t* count, int reset);
 /* Which row pass ed_apply_H runs for `dtype` on this context: 0 = the
  * plain per-row kernel (the class-sorted kernels do not apply), 1 = the
- * single-row pass (k_row5), 2 = the staged-source row pass (k_rowx), 3 =
- * k_row5 without cross terms followed by their scatter-add (k_xpush);
- * negative: ed_build_local_ops has not run. */
+ * class-sorted row pass (k_row5); negative: ed_build_local_ops has not run. */
 int ed_row_pass(const ed_ctx* ctx, ed_dtype dtype);
 
 /* ---- queries ---------------------------------------------------------- */
@@ -347,6 +344,9 @@ ed_status ed_blocks(const ed_ctx* ctx, int* s, int64_t* dA, int64_t* dB, int64_t
 /* bit-string keys (oracle convention: spin key bit i = site i; Hubbard
  * key = up | dw << n_sites) of the global indices [start, start+count), host. */
 ed_status ed_state_keys(const ed_ctx* ctx, int64_t start, int64_t count, uint64_t* keys);
+/* lattice site of each side-local bit: side 0 = A, 1 = B; sites: host array
+ * of at least n_sites ints, *n_bits: bits on that side. */
+ed_status ed_side_sites(const ed_ctx* ctx, int side, int* sites, int* n_bits);
 /* fill x (device, ed_dim elements of dtype) with the key-indexed SplitMix64
  * values U[-1,1) for `seed` (unnormalised); enqueued on stream. */
 ed_status ed_random_vector(ed_ctx* ctx, uint64_t seed, void* x, ed_dtype dtype, void* stream);

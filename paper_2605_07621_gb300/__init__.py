@@ -13,9 +13,6 @@ from .ed import (  # noqa: E402,F401
     OPS_DEFAULT,
     OPS_FORCE_CSR,
     OPS_FORCE_DENSE,
-    OPS_ROW_SINGLE,
-    OPS_ROW_STAGED,
-    OPS_ROW_PUSH,
     Batch,
     batch_apply,
     batch_create,
@@ -38,5 +35,4 @@ from ._lib import EDError  # noqa: E402,F401
 
 __all__ = ["Batch", "batch_apply", "batch_create", "batch_lanczos", "Context", "DenseOperator", "LanczosResult", "Server", "apply_H", "apply_H_noalloc", "build_local_ops", "build_sectors",
            "EntanglementSpectrum", "entanglement_spectrum", "lanczos_gf",
-           "lanczos_ground", "random_vector", "EDError", "OPS_DEFAULT", "OPS_FORCE_CSR", "OPS_FORCE_DENSE",
-           "OPS_ROW_SINGLE", "OPS_ROW_STAGED", "OPS_ROW_PUSH"]
+           "lanczos_ground", "random_vector", "EDError", "OPS_DEFAULT", "OPS_FORCE_CSR", "OPS_FORCE_DENSE"]

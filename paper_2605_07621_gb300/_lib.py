@@ -98,6 +98,7 @@ SIGNATURES = [
     ("ed_num_blocks", c_int, [c_void_p]),
     ("ed_blocks", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("ed_state_keys", c_int, [c_void_p, c_int64, c_int64, c_void_p]),
+    ("ed_side_sites", c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     ("ed_random_vector", c_int, [c_void_p, c_uint64, c_void_p, c_int, c_void_p]),
     ("ed_device_bytes", c_int64, [c_void_p]),
     ("ed_destroy", None, [c_void_p]),

@@ -467,7 +467,7 @@ extern "C" ed_status ed_apply_H(ed_ctx* c, const void* x, void* y, ed_dtype dt, 
   const char* xb = (const char*)x;
   const char* yb = (const char*)y;
   if (c->D > 0 && xb < yb + c->D * es && yb < xb + c->D * es) { set_error("x and y overlap"); return ED_EINVAL; }
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   return apply_H_impl(c, x, y, dt, (cudaStream_t)stream);
 }
 
@@ -475,6 +475,6 @@ extern "C" ed_status ed_random_vector(ed_ctx* c, uint64_t seed, void* x, ed_dtyp
   ED_TRY(check_ready(c));
   if (dt != ED_F64 && dt != ED_F32) { set_error("bad dtype %d", (int)dt); return ED_EINVAL; }
   if (c->D > 0 && !x) { set_error("x is NULL"); return ED_EINVAL; }
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   return random_vector_impl(c, seed, x, dt, (cudaStream_t)stream);
 }

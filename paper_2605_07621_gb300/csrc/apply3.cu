@@ -7,18 +7,17 @@
 //         pipe and rounded once back to FP64.  FP64 adds and FP64
 //         conversions run at about 0.5 T/s on this GPU, the integer pipe at
 //         tens of T/s, so no FP64 instruction is issued per matrix element.
-// Row pass: psi_s[a,:] is staged in shared memory by bulk TMA copies, then
-// each column b sums, class by class, the H_B neighbours (16-bit column
-// indices) and the cross-cut gathers, plus the diagonal.  Three forms of the
-// cross terms: k_row5 (here, default) gathers them from x in global memory;
-// k_rowx (rowx.cuh) stages each cross term's source row in shared memory;
-// k_xpush (here) pushes them from staged source rows with atomic adds.
+// Row pass (k_row5): the diagonal, the H_B (column-mixing) term and the
+// cross-cut terms of whole rows.  psi_s[a,:] is staged in shared memory by
+// bulk TMA copies, then each column b sums, class by class, its H_B
+// neighbours (16-bit column indices) and the cross-cut gathers from x in
+// global memory, plus the diagonal.
 // Panel pass: the H_A (row-mixing) term over column panels that stay
 // resident in L2.
 #include <mutex>
 #include <type_traits>
 
-#include "rowx.cuh"
+#include "apply3.cuh"
 
 namespace edk {
 
@@ -473,147 +472,6 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
 }
 
 
-// ---------------------------------------------------------------- cross terms by scatter-add
-//
-// Cross-cut terms pushed from their source rows (the transpose of the
-// gather in k_row5): a CTA stages one row x_s'[a',:] in shared memory and,
-// for every A cross site ia whose flip leads to an existing row a of block
-// s = s' -+ 1, forms the whole contribution of that source row to y_s[a,:]
-// -- for each column b, the bonds (ia, ib) valid at (a, b) gather
-// x_s'[a', mapB_ib(b)] from shared memory -- and adds it to y with
-// coalesced atomic adds (exact and order-independent on 64-bit integers).
-// Source rows are taken in the work-list order, whose target rows share
-// the untouched A bits and so stay L2-resident while they receive their
-// contributions.  y must already hold the other terms (row pass with
-// keep_fixed for the fixed-point path).
-template <class S>
-__device__ __forceinline__ void atomic_acc(S* p, S v);
-template <>
-__device__ __forceinline__ void atomic_acc<float>(float* p, float v) { atomicAdd(p, v); }
-template <>
-__device__ __forceinline__ void atomic_acc<double>(double* p, double v) { atomicAdd(p, v); }
-template <>
-__device__ __forceinline__ void atomic_acc<long long>(long long* p, long long v) {
-  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
-
-template <class Pol>
-__global__ void __launch_bounds__(kRowThreads, 2)
-    k_xpush(P3 p, const int2* __restrict__ rows, long long n_rows, const typename Pol::S* __restrict__ x,
-            typename Pol::S* __restrict__ y, long long stage_elems, int* err) {
-  using S = typename Pol::S;
-  extern __shared__ __align__(16) unsigned char smemp[];
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smemp);
-  S* buf = reinterpret_cast<S*>(smemp + 128);
-  __shared__ long long s_off[32];  // per A cross site: target row's first element (-1: none)
-  __shared__ int s_blk[32];
-  __shared__ int s_pad;
-  constexpr int V = 16 / (int)sizeof(S);
-  const Dev3& t = p.t;
-  if (threadIdx.x == 0) {
-    bar_init(&bar[0]);
-    bar_fence_init();
-  }
-  __syncthreads();
-  unsigned phase = 0;
-  for (long long g = blockIdx.x; g < n_rows; g += gridDim.x) {
-    const int2 w = rows[g];
-    const DevBlock bl = p.blocks[w.x];
-    const long long gA = bl.gA0 + w.y;
-    const int dB = (int)bl.dB;
-    const long long g0 = bl.off + (long long)w.y * dB, gend = g0 + dB;
-    const long long gal = (g0 + V - 1) / V * V, galend = gend / V * V;
-    const int pad = (int)(g0 % V);
-    if (threadIdx.x == 0) {
-      s_pad = pad;
-      proxy_fence();
-      if (galend > gal) {
-        const unsigned bytes = (unsigned)((galend - gal) * (long long)sizeof(S));
-        bar_expect(&bar[0], bytes);
-        bulk_g2s(buf + pad + (gal - g0), x + gal, bytes, &bar[0]);
-      } else {
-        bar_arrive(&bar[0]);
-      }
-    }
-    if (galend > gal) {
-      for (long long q = g0 + threadIdx.x; q < gal; q += blockDim.x) buf[pad + (q - g0)] = x[q];
-      for (long long q = galend + threadIdx.x; q < gend; q += blockDim.x) buf[pad + (q - g0)] = x[q];
-    } else {
-      for (long long q = g0 + threadIdx.x; q < gend; q += blockDim.x) buf[pad + (q - g0)] = x[q];
-    }
-    if (threadIdx.x < 32) {
-      const int ia = threadIdx.x;
-      long long off = -1;
-      int tb = -1;
-      if (ia < t.n_ia && t.ia_mask[ia]) {
-        const int k = __ffs(t.ia_mask[ia]) - 1;
-        const unsigned pa = t.A_pack[gA];
-        const int sb = ((pa >> k) & 1u) ? bl.nbr_lo : bl.nbr_hi;
-        if (sb >= 0) {
-          const unsigned rr = t.mapA[(long long)ia * t.A_total + gA];
-          if (rr != 0xFFFFu) {
-            const DevBlock so = p.blocks[sb];
-            off = so.off + (long long)rr * so.dB;
-            tb = sb;
-          }
-        }
-      }
-      s_off[ia] = off;
-      s_blk[ia] = tb;
-    }
-    const bool ok = bar_wait(&bar[0], phase);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
-      bar_wait(&bar[0], phase);
-      return;
-    }
-    phase ^= 1;
-    const S* xs = buf + s_pad;
-    const unsigned pa = t.A_pack[gA];
-    for (int ia = 0; ia < t.n_ia; ++ia) {
-      const long long off = s_off[ia];
-      if (off < 0) continue;
-      const DevBlock tbk = p.blocks[s_blk[ia]];
-      const unsigned km = t.ia_mask[ia];
-      // bit ia of the target row is the complement of the source row's
-      const unsigned abit_t = ((pa >> (__ffs(km) - 1)) & 1u) ^ 1u;
-      S* yr = y + off;
-      const int dBt = (int)tbk.dB;
-      const long long gB0 = tbk.gB0;
-      for (int b = threadIdx.x; b < dBt; b += blockDim.x) {
-        const long long gB = gB0 + b;
-        const unsigned pb = t.B_pack[gB] ^ (abit_t ? 0xFFFFFFFFu : 0u);
-        S v = 0;
-        bool any = false;
-        unsigned kk = km;
-        while (kk) {
-          const int k = __ffs(kk) - 1;
-          kk &= kk - 1;
-          if ((pb >> k) & 1u) {
-            v += Pol::bw(t, k) * xs[__ldg(t.mapB + (long long)t.bond_ib[k] * t.B_total + gB)];
-            any = true;
-          }
-        }
-        if (any) atomic_acc<S>(yr + b, v);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// 64-bit partial sums of the rows of blocks without H_A -> FP64 (after the
-// cross terms were pushed; blocks with H_A are converted by the panel pass)
-__global__ void k_finalize_plain(P3 p, long long* __restrict__ y, const int* __restrict__ emax) {
-  const int e2 = out_exp(p.t, emax);
-  for (int bi = blockIdx.x; bi < p.nblk; bi += gridDim.x) {
-    const DevBlock bl = p.blocks[bi];
-    if (bl.has_hA) continue;
-    const long long n = bl.dA * bl.dB;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x)
-      reinterpret_cast<double*>(y)[bl.off + i] = from_fixed(y[bl.off + i], e2);
-  }
-}
-
 static P3 make_p3(const ed_ctx* c) {
   P3 p;
   p.t = c->t3;
@@ -670,44 +528,6 @@ struct ProfMarks {
   }
 };
 
-static bool rx_plan(const ed_ctx* c, size_t es, RxPlan* out) {
-  if (!c->d_rowx || c->n_rowx <= 0 || c->n_rowx > INT32_MAX) return false;
-  long long mdb = 1;
-  for (const auto& b : c->blocks) mdb = std::max<long long>(mdb, b.dB);
-  if (!(c->ops_flags & ED_OPS_ROW_STAGED)) return false;
-  for (int ia = 0; ia < c->t3.n_ia; ++ia)
-    if (__builtin_popcount(c->t3.ia_mask[ia]) > kRxMaxBondsPerSite) return false;
-  if (c->t3.n_ia > 31) return false;
-  const int cons = (es == 4 ? rx_threads<float>() : rx_threads<double>()) - 32;
-  const long long need = (mdb + cons - 1) / cons;
-  int ncol = 0;
-  for (int v : kRxCols)
-    if (!ncol && need <= v) ncol = v;
-  if (!ncol || (es == 4 && ncol > 13)) return false;
-  int optin = 0;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  const long long stage = ((mdb + 1 + 16 / (long long)es + 15) / 16) * 16;
-  const size_t head = 64 + kRxMaxBuf * sizeof(RxDesc);
-  const long long per = stage * (long long)es;
-  const long long nb = std::min<long long>(kRxMaxBuf, ((long long)optin - (long long)head) / per);
-  if (nb < 2) return false;
-  out->ncol = ncol;
-  out->nbuf = (int)nb;
-  out->stage = stage;
-  out->smem = head + (size_t)nb * (size_t)per;
-  return true;
-}
-
-// cross terms by scatter-add (ED_OPS_ROW_PUSH): spin models with cross
-// bonds and a work list
-static bool push_usable(const ed_ctx* c) {
-  return (c->ops_flags & ED_OPS_ROW_PUSH) && c->d_rowx && c->n_rowx == c->n_rows && c->kind == ED_SPIN &&
-         !c->cross.empty();
-}
-
 template <class Pol>
 static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y, const int* emax, cudaStream_t st,
                         ProfMarks& pm) {
@@ -722,33 +542,13 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
   const size_t smem = v3_smem(c, sizeof(typename Pol::S), &se);
   const int sms = n_sms(c->device);
   pm.mark(2, st);
-  RxPlan rx;
-  const bool push = push_usable(c);
-  if (!push && rx_plan(c, sizeof(typename Pol::S), &rx)) {
-    ED_CUDA_TRY(cudaMemsetAsync(c->d_sched, 0, sizeof(int), st));
-    ED_TRY(rx_launch(c, p, rx, x, y, emax, st));
-  } else {
-    // push mode: the row pass leaves the cross terms (and, in fixed point,
-    // the final rounding) to k_xpush / the panel pass / k_finalize_plain
-    P3 q = p;
-    if (push) {
-      q.ncross = 0;
-      q.keep_fixed = 1;
-    }
+  {
     auto kern = k_row5<Pol, R, NT, CPS>;
     ED_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long* gs = R == 4 ? c->d_grp4_start : R == 2 ? c->d_grp2_start : c->d_row_start;
     const long long ng = R == 4 ? c->n_grp4 : R == 2 ? c->n_grp2 : c->n_rows;
     const long long grid = std::min<long long>(ng, (long long)sms * CPS);
-    kern<<<(unsigned)grid, NT, smem, st>>>(q, gs, ng, x, y, emax, se, c->d_err);
-    ED_CUDA_TRY(cudaGetLastError());
-    if (push) {
-      const size_t smem1 = 128 + (size_t)se * sizeof(typename Pol::S);
-      auto kx = k_xpush<Pol>;
-      ED_CUDA_TRY(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-      const long long gx = std::min<long long>(c->n_rowx, (long long)sms * 2);
-      kx<<<(unsigned)gx, kRowThreads, smem1, st>>>(p, c->d_rowx, c->n_rowx, x, y, se, c->d_err);
-    }
+    kern<<<(unsigned)grid, NT, smem, st>>>(p, gs, ng, x, y, emax, se, c->d_err);
   }
   ED_CUDA_TRY(cudaGetLastError());
   pm.mark(3, st);
@@ -763,12 +563,6 @@ static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y,
     else
       k_panel4<Pol, 4, 4><<<(unsigned)g2, 256, 0, st>>>(p, c->d_panel_items, c->n_panel_items, x, y, emax);
     ED_CUDA_TRY(cudaGetLastError());
-  }
-  if constexpr (sizeof(typename Pol::S) == 8 && !std::is_floating_point<typename Pol::S>::value) {
-    if (push) {
-      k_finalize_plain<<<(unsigned)std::max(1, std::min(p.nblk, sms)), 256, 0, st>>>(p, (long long*)y, emax);
-      ED_CUDA_TRY(cudaGetLastError());
-    }
   }
   return ED_OK;
 }
@@ -914,7 +708,7 @@ extern "C" ed_status ed_apply_H_noalloc(ed_ctx* c, const void* x, void* y, void*
               "32 cross bonds and 65534 states per side charge)");
     return ED_EUNSUPPORTED;
   }
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   ProfMarks pm;  // no profiling events here
   if (!c->dyadic) return run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st, pm);
@@ -928,10 +722,7 @@ extern "C" ed_status ed_apply_H_noalloc(ed_ctx* c, const void* x, void* y, void*
 extern "C" int ed_row_pass(const ed_ctx* c, ed_dtype dt) {
   if (!c || !c->ops_built) return -1;
   if (!v3_usable(c, dt, (const void*)(uintptr_t)256)) return 0;  // any 16-byte aligned x
-  if (push_usable(c)) return 3;
-  RxPlan rx;
-  const size_t es = dt == ED_F32 ? 4 : 8;
-  return rx_plan(c, es, &rx) ? 2 : 1;
+  return 1;
 }
 
 extern "C" ed_status ed_profile_enable(ed_ctx* c, int enable) {

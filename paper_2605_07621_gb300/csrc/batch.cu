@@ -317,7 +317,7 @@ BatchEngine::~BatchEngine() {
 
 ed_status BatchEngine::init(int device, size_t arena_bytes, int max_slots, int max_iter) {
   device_ = device;
-  ED_CUDA_TRY(cudaSetDevice(device));
+  ED_DEVICE_SCOPE(device);
   if (cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     cudaGetLastError();
     sms_ = 148;

@@ -330,7 +330,7 @@ extern "C" ed_status ed_dense_apply(ed_dense* d, const double* x, double* y, voi
   if (!d) { set_error("dense operator is NULL"); return ED_EINVAL; }
   if (!x || !y) { set_error("x or y is NULL"); return ED_EINVAL; }
   if (x < y + d->D && y < x + d->D) { set_error("x and y overlap"); return ED_EINVAL; }
-  ED_CUDA_TRY(cudaSetDevice(d->device));
+  ED_DEVICE_SCOPE(d->device);
   cudaStream_t st = (cudaStream_t)stream;
   for (const auto& s : d->stages) {
     k_gemm_batch<<<(unsigned)s.tiles, 256, 0, st>>>(d->d_probs + s.first, s.count, x, y);

@@ -494,7 +494,7 @@ extern "C" ed_status ed_lanczos_ground(ed_ctx* c, const ed_lanczos_opts* opts_in
     return ED_EINVAL;
   }
   if (c->D < 1) { set_error("empty sector"); return ED_EINVAL; }
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   ED_TRY(ensure_scratch(c));
   cudaStream_t st = (cudaStream_t)o.stream;
   const long long n = c->D;
@@ -708,7 +708,7 @@ extern "C" ed_status ed_lanczos_gf(ed_ctx* c, const void* psi0, double e0, int s
     set_error("bad Green's function arguments");
     return ED_EINVAL;
   }
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   ED_TRY(ensure_scratch(c));
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf mem;

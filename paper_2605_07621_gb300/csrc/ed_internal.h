@@ -33,7 +33,50 @@ void set_error(const char* fmt, ...);
     if (s_ != ED_OK) return s_;      \
   } while (0)
 
+// Makes `dev` the current device for the scope of one entry point and puts
+// the caller's current device back on exit, so no call changes the calling
+// thread's current device.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) {
+      cudaGetLastError();
+      prev_ = -1;
+    }
+    if (prev_ != dev) {
+      err_ = cudaSetDevice(dev);
+      if (err_ != cudaSuccess) cudaGetLastError();
+      else switched_ = true;
+    }
+  }
+  ~DeviceGuard() {
+    if (switched_ && prev_ >= 0) cudaSetDevice(prev_);
+  }
+  ed_status status() const {
+    if (err_ == cudaSuccess) return ED_OK;
+    set_error("cudaSetDevice failed: %s", cudaGetErrorString(err_));
+    return ED_ECUDA;
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool switched_ = false;
+  cudaError_t err_ = cudaSuccess;
+};
+
+#define ED_DEVICE_SCOPE(dev)                 \
+  ::edk::DeviceGuard ed_dev_guard_(dev);     \
+  do {                                       \
+    ed_status s_ = ed_dev_guard_.status();   \
+    if (s_ != ED_OK) return s_;              \
+  } while (0)
+
 int64_t binom(int n, int k);
+// side-local bit orders of a spin model (side A: sites on a cross-cut bond
+// low; side B: those sites high)
+void order_spin_sides(const ed_model_desc* m, std::vector<int>& sitesA, std::vector<int>& sitesB);
 // colex (combinadic) rank of an n-bit string among strings of equal popcount:
 // rank(x) = sum_j C(p_j, j+1) over the set-bit positions p_0 < p_1 < ...
 int64_t combinadic_rank(uint64_t x);
@@ -219,9 +262,6 @@ struct ed_ctx {
   long long n_grp4 = 0;
   long long n_panel_items = 0;
   int* d_err = nullptr;              // set by kernels whose bounded waits ran out
-  int2* d_rowx = nullptr;            // (block, row) work list of the staged-source row pass
-  long long n_rowx = 0;
-  int* d_sched = nullptr;            // work counter of that pass (cleared before each launch)
   // class-sorted path
   bool v3_ok = false;                // tables below are valid
   bool dyadic = false;               // FP64 apply may use exact fixed point

@@ -193,7 +193,7 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     set_error("%s", S.why.c_str());
     return ED_EUNSUPPORTED;
   }
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   ED_TRY(ensure_scratch(c));
   cudaStream_t st = (cudaStream_t)stream;
   Handle H;

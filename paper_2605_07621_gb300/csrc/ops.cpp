@@ -326,45 +326,18 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   t.A_total = c->A.total();
   t.B_total = c->B.total();
   ED_TRY(dev_alloc(c, (void**)&c->d_exp, 64));
-  // Work list of the staged-source row pass (spin models with cross-cut
-  // bonds): every row of every block, ordered by the A bits that no cross
-  // bond touches.  A cross term flips exactly one touched A bit, so the
-  // source rows of a row share its untouched bits: rows taken in this order
-  // find their sources among rows read moments earlier (resident in L2).
-  if (c->kind == ED_SPIN && !c->cross.empty()) {
-    uint32_t touched = 0;
-    for (int q : c->crossA_bits) touched |= 1u << q;
-    std::vector<std::pair<uint64_t, int2>> order;
-    order.reserve((size_t)c->n_rows);
-    for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
-      const Block& b = c->blocks[bi];
-      for (int64_t a = 0; a < b.dA; ++a) {
-        const uint32_t st = c->A.states[(size_t)(b.gA0 + a)];
-        const uint64_t key = ((uint64_t)(st & ~touched) << 32) | ((uint64_t)bi << 16) | (uint64_t)a;
-        order.push_back({key, make_int2((int)bi, (int)a)});
-      }
-    }
-    std::sort(order.begin(), order.end(), [](const auto& u, const auto& v) { return u.first < v.first; });
-    std::vector<int2> rows(order.size());
-    for (size_t i = 0; i < order.size(); ++i) rows[i] = order[i].second;
-    c->n_rowx = (long long)rows.size();
-    ED_TRY(upload(c, &c->d_rowx, rows));
-    std::vector<int> z(4, 0);
-    ED_TRY(upload(c, &c->d_sched, z));
-  }
   c->v3_ok = true;
   return ED_OK;
 }
 
 extern "C" ed_status ed_build_local_ops(ed_ctx* c, int flags) {
   if (!c) { set_error("ctx is NULL"); return ED_EINVAL; }
-  const int rowf = flags & (ED_OPS_ROW_SINGLE | ED_OPS_ROW_STAGED | ED_OPS_ROW_PUSH);
-  if (flags < 0 || flags > 31 || (flags & 3) == 3 || (rowf & (rowf - 1)) != 0) {
+  if (flags < 0 || flags > 3 || flags == 3) {
     set_error("bad flags %d", flags);
     return ED_EINVAL;
   }
   if (c->ops_built) return ED_OK;
-  ED_CUDA_TRY(cudaSetDevice(c->device));
+  ED_DEVICE_SCOPE(c->device);
   HostSideOps ha, hb;
   ED_TRY(build_side_ops(c, c->A, c->bondsA, true, ha));
   ED_TRY(build_side_ops(c, c->B, c->bondsB, false, hb));

@@ -90,6 +90,30 @@ static void build_side(Side& sd, int n, const std::vector<int>& sites, const std
   sd.start[n + 1] = (int64_t)sd.states.size();
 }
 
+// Side-local bit order of a spin model's two sides.  On side B the sites
+// on a cross-cut bond take the high bits: the columns with one
+// configuration of those sites are then a contiguous run, and flipping one
+// of them maps the run onto a run of the neighbouring block shifted as a
+// whole, so the cross-term gathers of consecutive columns read consecutive
+// elements.  On side A they take the low bits: consecutive rows then differ
+// at the cut sites and a row group often shares cross-term source rows.
+void order_spin_sides(const ed_model_desc* m, std::vector<int>& sitesA, std::vector<int>& sitesB) {
+  const int n = m->n_sites;
+  std::vector<char> atCut(n, 0), inA(n, 0);
+  for (int i = 0; i < n; ++i) inA[i] = (char)((m->cut_mask >> i) & 1ULL);
+  for (int b = 0; b < m->n_bonds; ++b) {
+    const int i = m->bi[b], j = m->bj[b];
+    if (inA[i] != inA[j]) atCut[i] = atCut[j] = 1;
+  }
+  sitesA.clear();
+  sitesB.clear();
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < n; ++i) {
+      if (inA[i] && atCut[i] == 1 - pass) sitesA.push_back(i);
+      if (!inA[i] && atCut[i] == pass) sitesB.push_back(i);
+    }
+}
+
 }  // namespace edk
 
 using namespace edk;
@@ -155,25 +179,9 @@ extern "C" ed_status ed_build_sectors(const ed_model_desc* m, ed_ctx** out) {
   std::vector<int> sitesA, sitesB, local(n, -1);
   std::vector<char> sideOf(n, 0);  // 0 = A, 1 = B
   if (c->kind == ED_SPIN) {
-    // side-local bit order.  On side B the sites on a cross-cut bond take the
-    // high bits: the columns with one configuration of those sites are then a
-    // contiguous run, and flipping one of them maps the run onto a run of the
-    // neighbouring block shifted as a whole, so the cross-term gathers of
-    // consecutive columns read consecutive elements.  On side A they take the
-    // low bits: consecutive rows then differ at the cut sites and a row group
-    // often shares cross-term source rows.
-    std::vector<char> atCut(n, 0);
-    for (int b = 0; b < nb; ++b) {
-      const int i = m->bi[b], j = m->bj[b];
-      if (((m->cut_mask >> i) & 1ULL) != ((m->cut_mask >> j) & 1ULL)) atCut[i] = atCut[j] = 1;
-    }
-    for (int pass = 0; pass < 2; ++pass)
-      for (int i = 0; i < n; ++i) {
-        const bool inA = (m->cut_mask >> i) & 1ULL;
-        if (atCut[i] != (inA ? 1 - pass : pass)) continue;
-        if (inA) { local[i] = (int)sitesA.size(); sitesA.push_back(i); sideOf[i] = 0; }
-        else { local[i] = (int)sitesB.size(); sitesB.push_back(i); sideOf[i] = 1; }
-      }
+    order_spin_sides(m, sitesA, sitesB);
+    for (size_t p = 0; p < sitesA.size(); ++p) { local[sitesA[p]] = (int)p; sideOf[sitesA[p]] = 0; }
+    for (size_t q = 0; q < sitesB.size(); ++q) { local[sitesB[q]] = (int)q; sideOf[sitesB[q]] = 1; }
   } else {
     for (int i = 0; i < n; ++i) { sitesA.push_back(i); sitesB.push_back(i); local[i] = i; }
   }
@@ -340,6 +348,17 @@ extern "C" ed_status ed_state_keys(const ed_ctx* c, int64_t start, int64_t count
     int64_t r = loc / bl.dB, col = loc % bl.dB;
     keys[g - start] = state_key(c, c->A.states[bl.gA0 + r], c->B.states[bl.gB0 + col]);
   }
+  return ED_OK;
+}
+
+extern "C" ed_status ed_side_sites(const ed_ctx* c, int side, int* sites, int* n_bits) {
+  if (!c || !sites || !n_bits || (side != 0 && side != 1)) {
+    set_error("ed_side_sites: bad arguments");
+    return ED_EINVAL;
+  }
+  const Side& sd = side == 0 ? c->A : c->B;
+  for (int p = 0; p < sd.n; ++p) sites[p] = sd.sites[p];
+  *n_bits = sd.n;
   return ED_OK;
 }
 

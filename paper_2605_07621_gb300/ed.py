@@ -19,9 +19,6 @@ _MODES = {"f64": L.ED_LZ_F64, "f32": L.ED_LZ_F32, "mixed": L.ED_LZ_MIXED}
 OPS_DEFAULT = 0
 OPS_FORCE_CSR = 1
 OPS_FORCE_DENSE = 2
-OPS_ROW_SINGLE = 4
-OPS_ROW_STAGED = 8
-OPS_ROW_PUSH = 16
 
 
 def _stream_handle(stream):
@@ -90,6 +87,13 @@ class Context:
         L.check(L.load().ed_state_keys(self._h, int(start), int(count), keys.ctypes.data))
         return keys[:count]
 
+    def side_sites(self, side: int) -> list:
+        """Lattice site of each side-local bit of side 0 (A) or 1 (B)."""
+        buf = (ctypes.c_int * 64)()
+        n = ctypes.c_int()
+        L.check(L.load().ed_side_sites(self._h, int(side), buf, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
     @property
     def device_bytes(self) -> int:
         return int(L.load().ed_device_bytes(self._h))
@@ -104,7 +108,7 @@ class Context:
 
         dt = L.ED_F32 if dtype in (torch.float32, "f32") else L.ED_F64
         k = int(L.load().ed_row_pass(self._h, dt))
-        return {0: "k_apply_rows", 1: "k_row5", 2: "k_rowx", 3: "k_row5+k_xpush"}.get(k, "none")
+        return {0: "k_apply_rows", 1: "k_row5"}.get(k, "none")
 
     def profile_read(self, reset: bool = True):
         """(ms per stage [exp_max, to_fixed, row pass, panel pass], number of applies)."""

@@ -79,8 +79,8 @@ def test_blocks_and_keys_match_oracle(edlib, oracle_mod, name):
     okeys = oracle_mod.sector_keys(m)
     np.testing.assert_array_equal(np.sort(keys), okeys)
     # rows ascend within each block (combinadic order of the side-local bit
-    # words), columns too.  Side-local bits: on side A the sites on a
-    # cross-cut bond come first (low bits), on side B last (high bits)
+    # words), columns too.  Side-local bits (ed_side_sites): on side A the
+    # sites on a cross-cut bond come first (low bits), on side B last (high bits)
     if m.kind == "spin":
         inA = [(m.cut_mask >> i) & 1 for i in range(m.n_sites)]
         cut = [False] * m.n_sites
@@ -89,6 +89,7 @@ def test_blocks_and_keys_match_oracle(edlib, oracle_mod, name):
                 cut[i] = cut[j] = True
         sa = [i for i in range(m.n_sites) if inA[i] and cut[i]] + [i for i in range(m.n_sites) if inA[i] and not cut[i]]
         sb = [i for i in range(m.n_sites) if not inA[i] and not cut[i]] + [i for i in range(m.n_sites) if not inA[i] and cut[i]]
+        assert ctx.side_sites(0) == sa and ctx.side_sites(1) == sb
 
         def local(k, sites):
             return sum(((int(k) >> i) & 1) << p for p, i in enumerate(sites))
@@ -107,6 +108,10 @@ def test_j1j2_4x8_structure(edlib):
     assert dA.max() * dB.max() == 165636900
     w = dA * dB / ctx.dim
     assert abs(1.0 / np.sum(w ** 2) - 5.11) < 0.01
+    # side B (columns x = 4..7): the 8 sites of the columns x = 5, 6 take the
+    # low bits, the 8 sites on cross-cut bonds (x = 4, 7) the high bits
+    assert sorted(ctx.side_sites(1)[:8]) == list(range(20, 28))
+    assert sorted(ctx.side_sites(1)[8:]) == list(range(16, 20)) + list(range(28, 32))
 
 
 def test_malformed_models_rejected(edlib):

@@ -193,47 +193,56 @@ EXTRA_CROSS = {
 }
 
 
-@pytest.mark.parametrize("name", CROSS_MODELS + list(EXTRA_CROSS))
-def test_row_pass_variants(ed, oracle_mod, name):
-    """The three ways of adding the cross terms (gathered from global
-    memory, gathered from source rows staged in shared memory, pushed from
-    staged source rows with atomic adds) against the oracle and against each
-    other: bit-identical in the exact fixed-point FP64 mode, FP32 within
-    summation-order rounding."""
+MORE_SPIN = {
+    # odd side sizes, a one-bit low half, two-bit sides
+    "xxz_9_cut5": lambda: W.xxz_chain(9, 1.0, 0.5, n_up=4, cut_mask=0b000011111),
+    "heis_6_cut2": lambda: W.heisenberg_chain(6, 1.0, 3, True, 0b000011),
+    "heis_5_cut2": lambda: W.heisenberg_chain(5, 1.0, 2, True, 0b00011),
+    # four value classes (J1 = 1, J2 = 0.5, jz != jxy): every class slot in use
+    "j1j2_xxz_4x4": lambda: W.Model("spin", 16, W.torus_j1j2_bonds(4, 4)[0] + W.torus_j1j2_bonds(4, 4)[1],
+                                    jxy=[1.0] * 32 + [0.5] * 32, jz=[0.75] * 32 + [0.25] * 32, n_up=7,
+                                    cut_mask=0xFF),
+    # non-dyadic couplings: the FP64 policy of the Kronecker pass
+    "j1j2_4x4_j2_03": lambda: W.j1j2_torus(4, 4, 1.0, 0.3, cut_mask=0xFF),
+    # three value classes on the bonds between the halves (ladder with rungs)
+    "ladder_2x6": lambda: W.Model("spin", 12, W.chain_bonds(6, True) + [(i + 6, (i + 1) % 6 + 6) for i in range(6)]
+                                  + [(i, i + 6) for i in range(6)],
+                                  jxy=[1.0] * 12 + [0.25] * 6, jz=[1.0] * 12 + [0.25] * 6, n_up=6,
+                                  cut_mask=0b000111000111),
+}
+
+
+@pytest.mark.parametrize("name", CROSS_MODELS + list(EXTRA_CROSS) + list(MORE_SPIN))
+def test_cross_term_models(ed, oracle_mod, name):
+    """Spin models with cross-cut bonds (crowded cuts, odd side sizes, four
+    value classes, non-dyadic couplings, ladders) against the oracle, FP64
+    and FP32, with the row pass each one gets."""
     import torch
 
-    m = MODELS[name] if name in MODELS else EXTRA_CROSS[name]()
+    if name in MODELS:
+        m = MODELS[name]
+    elif name in EXTRA_CROSS:
+        m = EXTRA_CROSS[name]()
+    else:
+        m = MORE_SPIN[name]()
     okeys = oracle_mod.sector_keys(m)
-    ys = {}
-    for flags in (ed.OPS_ROW_SINGLE, ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
-        ctx = ed.build_local_ops(ed.build_sectors(m), flags)
-        keys = ctx.state_keys()
-        pos = oracle_mod.find_keys(m, okeys, keys)
-        y_ref = oracle_mod.apply_H(m, okeys, W.start_values(okeys))[pos]
-        x64 = torch.tensor(W.start_values(keys), device="cuda")
-        for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
-            x = x64.to(dt)
-            y = torch.full_like(x, float("nan"))
-            ed.apply_H(ctx, x, y)
-            torch.cuda.synchronize()
-            yy = y.double().cpu().numpy()
-            assert np.linalg.norm(yy - y_ref) <= tol * np.linalg.norm(y_ref), (flags, dt)
-            ys[(flags, dt)] = yy
-    exact = _dyadic_spin(m)
-    for other in (ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
-        a, b = ys[(ed.OPS_ROW_SINGLE, torch.float64)], ys[(other, torch.float64)]
-        if exact:  # exact fixed point: any summation order gives the same bits
-            assert np.array_equal(a, b), other
-        else:
-            assert np.linalg.norm(a - b) <= 1e-14 * np.linalg.norm(a), other
-        a, b = ys[(ed.OPS_ROW_SINGLE, torch.float32)], ys[(other, torch.float32)]
-        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a), other
+    ctx = ed.build_local_ops(ed.build_sectors(m))
+    keys = ctx.state_keys()
+    pos = oracle_mod.find_keys(m, okeys, keys)
+    y_ref = oracle_mod.apply_H(m, okeys, W.start_values(okeys))[pos]
+    x64 = torch.tensor(W.start_values(keys), device="cuda")
+    for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        x = x64.to(dt)
+        y = torch.full_like(x, float("nan"))
+        ed.apply_H(ctx, x, y)
+        torch.cuda.synchronize()
+        yy = y.double().cpu().numpy()
+        assert np.linalg.norm(yy - y_ref) <= tol * np.linalg.norm(y_ref), (name, dt)
 
 
 def test_j1j2_4x7_full_parity(ed, oracle_mod):
     """J1-J2 4x7 torus, Sz=0, cut 14|14 (40,116,600 states, 15 blocks up to
-    3432 x 3432): every row-pass variant, FP64 and FP32, whole vector
-    against the oracle."""
+    3432 x 3432): FP64 and FP32, whole vector against the oracle."""
     import torch
 
     m = W.config_j1j2_4x7()
@@ -241,7 +250,7 @@ def test_j1j2_4x7_full_parity(ed, oracle_mod):
     xo = W.start_values(okeys)
     y_ref0 = oracle_mod.apply_H(m, okeys, xo)
     del xo
-    for flags in (ed.OPS_DEFAULT, ed.OPS_ROW_STAGED, ed.OPS_ROW_PUSH):
+    for flags in (ed.OPS_DEFAULT,):
         ctx = ed.build_local_ops(ed.build_sectors(m), flags)
         keys = ctx.state_keys()
         pos = oracle_mod.find_keys(m, okeys, keys)

@@ -1,9 +1,11 @@
 """ed_apply_H_noalloc: the H|psi> entry point for callers that cannot allocate
 device memory (its scratch is a fixed array inside the library).  Checked
-through the C ABI against ed_apply_H, within the FP64 tolerance of the other
-parity tests (relative L2 <= 1e-12), on two calls in a row with different
-inputs; the size limit is checked too.  Kept in its own file, collected
-last, and independent of the other tests' state."""
+through the C ABI against ed_apply_H and against the CPU oracle (outputs
+matched by bit-string key), within the FP64 tolerance of the other parity
+tests (relative L2 <= 1e-12), on two calls in a row with different inputs;
+the device's free memory is the same before and after those calls, and the
+size limit is checked too.  Kept in its own file, collected last, and
+independent of the other tests' state."""
 import ctypes
 
 import numpy as np
@@ -27,27 +29,47 @@ def ed():
     return ed
 
 
+def _model(name):
+    if name == "hub12":
+        return W.config_hub12()
+    if name == "heis16":
+        return W.config_heis16()
+    return W.j1j2_torus(4, 4, 1.0, 0.3, cut_mask=0xFF)  # J2/2 = 0.15: not dyadic, FP64 kernels
+
+
 @pytest.mark.parametrize("name", ["hub12", "heis16", "j1j2_4x4_nondyadic"])
-def test_noalloc_matches_apply_twice(ed, name):
+def test_noalloc_matches_apply_and_oracle_twice(ed, oracle_mod, name):
     import torch
 
-    if name == "hub12":
-        m = W.config_hub12()
-    elif name == "heis16":
-        m = W.config_heis16()
-    else:
-        m = W.j1j2_torus(4, 4, 1.0, 0.3, cut_mask=0xFF)  # J2/2 = 0.15: not dyadic, FP64 kernels
+    m = _model(name)
     ctx = ed.build_local_ops(ed.build_sectors(m))
+    okeys = oracle_mod.sector_keys(m)
+    pos = oracle_mod.find_keys(m, okeys, ctx.state_keys())
+    assert (pos >= 0).all()
+    xs, refs, ys = [], [], []
     for seed in (1, 2):
         x = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
         ed.random_vector(ctx, x, seed=seed)
         y_ref = torch.empty_like(x)
-        ed.apply_H(ctx, x, y_ref)
-        y = torch.full_like(x, float("nan"))
+        ed.apply_H(ctx, x, y_ref)  # the context's own scratch is allocated here, before the check below
+        xs.append(x)
+        refs.append(y_ref)
+        ys.append(torch.full_like(x, float("nan")))
+    ed.apply_H_noalloc(ctx, xs[0], ys[0])  # first call on the device: looks up the array's address
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for x, y in zip(xs, ys):
         ed.apply_H_noalloc(ctx, x, y)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0  # nothing allocated or freed by the two calls
+    for seed, x, y, y_ref in zip((1, 2), xs, ys, refs):
         err = (torch.linalg.norm(y - y_ref) / torch.linalg.norm(y_ref)).item()
         assert err <= TOL64, (name, seed, err)
+        xo = np.zeros(len(okeys))
+        xo[pos] = x.cpu().numpy()
+        yo = oracle_mod.apply_H(m, okeys, xo)[pos]
+        yg = y.cpu().numpy()
+        assert np.linalg.norm(yg - yo) <= TOL64 * np.linalg.norm(yo), (name, seed)
 
 
 def test_noalloc_rejects_oversized_sector(ed):
