@@ -6,115 +6,17 @@
 // matrices:
 //   Y_q  = H_L,q Psi_q + Psi_q H_R,q^T
 //   Y_q' += L_m,q Psi_q R_m,q^T,  q' = q + delta_m.
-// Every product runs in k_gemm_batch: FP64, one 64 x 64 output tile per CTA,
-// 64 x 16 operand slabs staged in shared memory, 4 x 4 outputs per thread,
-// all problems of one stage (all blocks q) in one launch.
+// Every product runs on the tensor cores in FP64-accurate digit-split form
+// (ozaki.cu): the side operators are split once at creation; each apply
+// splits the blocks of x (as rows for Psi H_R^T, as columns for H_L Psi and
+// L Psi) and the intermediate L Psi, and every stage is one launch over all
+// blocks.
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "krylov.h"
-
-namespace edk {
-namespace {
-
-constexpr int kDT = 64;  // output tile
-constexpr int kDK = 16;  // contraction depth per step
-
-// C (M x N, leading dimension ldc) = or += A B with A(i,k) = A[i*sai + k*sak]
-// and B(k,j) = B[k*sbk + j*sbj].  An operand is an absolute device address
-// (operators, scratch) or an offset into the x or y of the call, so the
-// problem lists are built once and stay on the device.
-enum { kAbs = 0, kX = 1, kY = 2 };
-struct GemmProblem {
-  const double* A;
-  const double* B;
-  double* C;
-  long long aoff, boff, coff;
-  int abase, bbase, cbase;
-  long long sai, sak, sbk, sbj, ldc;
-  int M, N, K;
-  int acc;         // 1: C += A B, 0: C = A B
-  int tiles_n;     // output tiles along N
-  long long tile0; // first tile of this problem in the launch
-};
-
-__device__ __forceinline__ const double* resolve(const double* p, long long off, int base, const double* x,
-                                                 const double* y) {
-  return base == kX ? x + off : base == kY ? y + off : p;
-}
-
-__global__ void __launch_bounds__(256) k_gemm_batch(const GemmProblem* __restrict__ probs, int nprob,
-                                                    const double* __restrict__ x, double* y) {
-  __shared__ double As[kDK][kDT + 1];
-  __shared__ double Bs[kDK][kDT + 1];
-  // problem of this tile (tile0 ascending)
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile0 <= (long long)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
-  const GemmProblem P = probs[lo];
-  const double* Ap = resolve(P.A, P.aoff, P.abase, x, y);
-  const double* Bp = resolve(P.B, P.boff, P.bbase, x, y);
-  double* Cp = const_cast<double*>(resolve(P.C, P.coff, P.cbase, x, y));
-  const long long t = (long long)blockIdx.x - P.tile0;
-  const long long i0 = (t / P.tiles_n) * kDT, j0 = (t % P.tiles_n) * kDT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
-  for (int k0 = 0; k0 < P.K; k0 += kDK) {
-    // A slab (64 rows x 16 k) and B slab (16 k x 64 columns); the faster
-    // index of each follows its contiguous direction
-    for (int e = threadIdx.x; e < kDT * kDK; e += blockDim.x) {
-      {
-        const bool kfast = P.sak == 1;
-        const int r = kfast ? e / kDK : e % kDT;
-        const int k = kfast ? e % kDK : e / kDT;
-        const long long gi = i0 + r, gk = k0 + k;
-        As[k][r] = (gi < P.M && gk < P.K) ? Ap[gi * P.sai + gk * P.sak] : 0.0;
-      }
-      {
-        const bool jfast = P.sbj == 1;
-        const int c = jfast ? e % kDT : e / kDK;
-        const int k = jfast ? e / kDT : e % kDK;
-        const long long gj = j0 + c, gk = k0 + k;
-        Bs[k][c] = (gj < P.N && gk < P.K) ? Bp[gk * P.sbk + gj * P.sbj] : 0.0;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kDK; ++k) {
-      double a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = As[k][ty + 16 * u];
-        b[u] = Bs[k][tx + 16 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const long long i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
-      if (i < P.M && j < P.N) {
-        double* c = Cp + i * P.ldc + j;
-        *c = P.acc ? *c + acc[u][v] : acc[u][v];
-      }
-    }
-}
-
-}  // namespace
-}  // namespace edk
+#include "ozaki.h"
 
 using namespace edk;
 
@@ -125,80 +27,63 @@ struct ed_dense {
   int64_t D = 0;
   struct Term {
     int delta;
-    std::vector<const double*> L, R;  // device, per source block q (nullptr: none)
-    std::vector<int64_t> toff;        // scratch offset of L Psi_q per q
+    std::vector<OzOperand> L, R;  // per source block q (R == 0: none)
+    std::vector<OzOperand> T;     // digit planes of L Psi_q
+    std::vector<int64_t> toff;    // scratch offset of L Psi_q per q
   };
-  std::vector<const double*> HL, HR;  // device, per block
+  std::vector<OzOperand> HL, HR;  // per block
+  std::vector<OzOperand> XA, XB;  // per block: Psi_q by rows, by columns
   std::vector<Term> terms;
   double* scratch = nullptr;
-  std::vector<void*> allocs;
-  // problem lists of the stages (device) and their tile counts
-  GemmProblem* d_probs = nullptr;
+  OzContext oz;
+  // device lists of the slicing and product stages
   struct Stage {
-    int first, count;
-    long long tiles;
+    int kind;  // 0: slice by rows, 1: slice by columns, 2: products
+    const void* list;
+    int count;
+    long long units;
   };
   std::vector<Stage> stages;
-  ~ed_dense() {
-    for (void* p : allocs) cudaFree(p);
-  }
 };
 
 namespace {
 
-ed_status dense_alloc(ed_dense* d, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error("cudaMalloc(%zu) for the dense-block operator failed: %s", bytes, cudaGetErrorString(e));
-    *p = nullptr;
-    return e == cudaErrorMemoryAllocation ? ED_ENOMEM : ED_ECUDA;
-  }
-  d->allocs.push_back(*p);
-  return ED_OK;
-}
+ed_status dense_alloc(ed_dense* d, void** p, size_t bytes) { return oz_alloc(&d->oz, p, bytes); }
 
-ed_status upload(ed_dense* d, const double* h, size_t n, const double** out) {
-  double* p = nullptr;
-  ED_TRY(dense_alloc(d, (void**)&p, n * sizeof(double)));
-  ED_CUDA_TRY(cudaMemcpy(p, h, n * sizeof(double), cudaMemcpyHostToDevice));
-  *out = p;
-  return ED_OK;
-}
-
-struct Opnd {
-  const double* p;
-  long long off;
-  int base;
-};
-Opnd abs_(const double* p) { return {p, 0, kAbs}; }
-Opnd xo(long long off) { return {nullptr, off, kX}; }
-Opnd yo(long long off) { return {nullptr, off, kY}; }
-
-GemmProblem problem(Opnd A, long long sai, long long sak, Opnd B, long long sbk, long long sbj, Opnd C, long long ldc,
-                    int M, int N, int K, int acc) {
-  GemmProblem p;
-  p.A = A.p;
-  p.B = B.p;
-  p.C = const_cast<double*>(C.p);
-  p.aoff = A.off;
-  p.boff = B.off;
-  p.coff = C.off;
-  p.abase = A.base;
-  p.bbase = B.base;
-  p.cbase = C.base;
-  p.sai = sai;
-  p.sak = sak;
-  p.sbk = sbk;
-  p.sbj = sbj;
+OzProblem oz_problem(const OzOperand& A, const OzOperand& B, double* C, long long coff, int cbase, long long ldc,
+                     int acc) {
+  OzProblem p;
+  p.mapA = A.map;
+  p.mapB = B.map;
+  p.ea = A.exps;
+  p.eb = B.exps;
+  p.C = C;
+  p.coff = coff;
+  p.cbase = cbase;
   p.ldc = ldc;
-  p.M = M;
-  p.N = N;
-  p.K = K;
+  p.M = A.R;
+  p.N = B.R;
+  p.K = A.K;
   p.acc = acc;
-  p.tiles_n = (N + kDT - 1) / kDT;
+  p.tiles_n = (B.R + kOzBN - 1) / kOzBN;
   p.tile0 = 0;
   return p;
+}
+
+OzSliceJob slice_job(const double* src, long long soff, int sbase, long long ld, int rows, int cols,
+                     const OzOperand& dst) {
+  OzSliceJob j;
+  j.src = src;
+  j.soff = soff;
+  j.sbase = sbase;
+  j.ld = ld;
+  j.rows = rows;
+  j.cols = cols;
+  j.dst = dst.slices;
+  j.exps = dst.exps;
+  j.Kpad = dst.Kpad;
+  j.first = 0;
+  return j;
 }
 
 }  // namespace
@@ -238,87 +123,114 @@ extern "C" ed_status ed_dense_create(int nq, const int64_t* chi, const double* c
     ~Guard() { delete d; }
   } g{d};
   if (cudaGetDevice(&d->device) != cudaSuccess) { cudaGetLastError(); d->device = 0; }
+  d->oz.device = d->device;
   d->nq = nq;
   d->chi.assign(chi, chi + nq);
   d->off.assign(nq + 1, 0);
   for (int q = 0; q < nq; ++q) d->off[q + 1] = d->off[q] + chi[q] * chi[q];
   d->D = d->off[nq];
+  // side operators split once: H_L as the left factor (rows = output rows),
+  // H_R as B^T of Psi H_R^T (rows = output columns)
   d->HL.resize(nq);
   d->HR.resize(nq);
+  d->XA.resize(nq);
+  d->XB.resize(nq);
   for (int q = 0; q < nq; ++q) {
-    ED_TRY(upload(d, HL[q], (size_t)(chi[q] * chi[q]), &d->HL[q]));
-    ED_TRY(upload(d, HR[q], (size_t)(chi[q] * chi[q]), &d->HR[q]));
+    const int c = (int)chi[q];
+    ED_TRY(oz_operand_host(&d->oz, HL[q], c, c, true, &d->HL[q]));
+    ED_TRY(oz_operand_host(&d->oz, HR[q], c, c, false, &d->HR[q]));
+    ED_TRY(oz_operand_device(&d->oz, c, c, true, &d->XA[q]));   // Psi_q: rows
+    ED_TRY(oz_operand_device(&d->oz, c, c, false, &d->XB[q]));  // Psi_q^T: columns of Psi_q
   }
   int64_t scratch = 0;
   for (int m = 0; m < n_terms; ++m) {
     ed_dense::Term t;
     t.delta = delta[m];
-    t.L.assign(nq, nullptr);
-    t.R.assign(nq, nullptr);
+    t.L.assign(nq, OzOperand{});
+    t.R.assign(nq, OzOperand{});
+    t.T.assign(nq, OzOperand{});
     t.toff.assign(nq, -1);
     int64_t s = 0;
     for (int q = 0; q < nq; ++q) {
       const double* l = Lm[(size_t)m * nq + q];
       if (!l) continue;
-      const int64_t ct = chi[q + delta[m]];
-      ED_TRY(upload(d, l, (size_t)(ct * chi[q]), &t.L[q]));
-      ED_TRY(upload(d, Rm[(size_t)m * nq + q], (size_t)(ct * chi[q]), &t.R[q]));
+      const int c = (int)chi[q], ct = (int)chi[q + delta[m]];
+      ED_TRY(oz_operand_host(&d->oz, l, ct, c, true, &t.L[q]));
+      ED_TRY(oz_operand_host(&d->oz, Rm[(size_t)m * nq + q], ct, c, false, &t.R[q]));
+      ED_TRY(oz_operand_device(&d->oz, ct, c, true, &t.T[q]));
       t.toff[q] = s;
-      s += ct * chi[q];
+      s += (int64_t)ct * c;
     }
     scratch = std::max(scratch, s);
     d->terms.push_back(std::move(t));
   }
   if (scratch > 0) ED_TRY(dense_alloc(d, (void**)&d->scratch, (size_t)scratch * sizeof(double)));
-  // problem lists: (1) Y_q = H_L Psi_q, (2) Y_q += Psi_q H_R^T, then per
-  // term (3) T_q = L Psi_q, (4) Y_{q+delta} += T_q R^T; each stage is one
-  // launch, whose problems write disjoint outputs
-  std::vector<GemmProblem> all;
-  auto close_stage = [&](size_t first) -> ed_status {
+  ED_TRY(oz_finish(&d->oz));
+  // stage lists (device, built once): each launch covers every block
+  auto put = [&](int kind, const void* host, size_t bytes, int count, long long units) -> ed_status {
+    void* dp = nullptr;
+    ED_TRY(dense_alloc(d, &dp, bytes));
+    ED_CUDA_TRY(cudaMemcpy(dp, host, bytes, cudaMemcpyHostToDevice));
+    d->stages.push_back({kind, dp, count, units});
+    return ED_OK;
+  };
+  auto slices = [&](std::vector<OzSliceJob>& v, bool by_cols) -> ed_status {
+    long long u = 0;
+    for (auto& j : v) {
+      j.first = u;
+      u += by_cols ? (j.cols + 31) / 32 : j.rows;
+    }
+    if (v.empty()) return ED_OK;
+    return put(by_cols ? 1 : 0, v.data(), v.size() * sizeof(OzSliceJob), (int)v.size(), u);
+  };
+  auto products = [&](std::vector<OzProblem>& v) -> ed_status {
     long long tiles = 0;
-    for (size_t i = first; i < all.size(); ++i) {
-      all[i].tile0 = tiles;
-      tiles += (long long)((all[i].M + kDT - 1) / kDT) * all[i].tiles_n;
+    for (auto& p : v) {
+      p.tile0 = tiles;
+      tiles += oz_tiles(p.M, p.N);
     }
     if (tiles > 0x7fffffffLL) {
       set_error("dense-block stage of %lld tiles exceeds one launch", tiles);
       return ED_EUNSUPPORTED;
     }
-    if (all.size() > first) d->stages.push_back({(int)first, (int)(all.size() - first), tiles});
-    return ED_OK;
+    if (v.empty()) return ED_OK;
+    return put(2, v.data(), v.size() * sizeof(OzProblem), (int)v.size(), tiles);
   };
-  size_t f = all.size();
-  for (int q = 0; q < nq; ++q) {
-    const long long c = chi[q];
-    all.push_back(problem(abs_(d->HL[q]), c, 1, xo(d->off[q]), c, 1, yo(d->off[q]), c, (int)c, (int)c, (int)c, 0));
+  {
+    std::vector<OzSliceJob> ja, jb;
+    for (int q = 0; q < nq; ++q) {
+      const int c = (int)chi[q];
+      ja.push_back(slice_job(nullptr, d->off[q], 1, c, c, c, d->XA[q]));
+      jb.push_back(slice_job(nullptr, d->off[q], 1, c, c, c, d->XB[q]));
+    }
+    ED_TRY(slices(ja, false));
+    ED_TRY(slices(jb, true));
   }
-  ED_TRY(close_stage(f));
-  f = all.size();
-  for (int q = 0; q < nq; ++q) {
-    const long long c = chi[q];
-    all.push_back(problem(xo(d->off[q]), c, 1, abs_(d->HR[q]), 1, c, yo(d->off[q]), c, (int)c, (int)c, (int)c, 1));
+  {
+    std::vector<OzProblem> s1, s2;
+    for (int q = 0; q < nq; ++q) {
+      const long long c = chi[q];
+      s1.push_back(oz_problem(d->HL[q], d->XB[q], nullptr, d->off[q], 1, c, 0));  // Y = H_L Psi
+      s2.push_back(oz_problem(d->XA[q], d->HR[q], nullptr, d->off[q], 1, c, 1));  // Y += Psi H_R^T
+    }
+    ED_TRY(products(s1));
+    ED_TRY(products(s2));
   }
-  ED_TRY(close_stage(f));
   for (const auto& t : d->terms) {
-    f = all.size();
+    std::vector<OzProblem> s3, s4;
+    std::vector<OzSliceJob> jt;
     for (int q = 0; q < nq; ++q) {
-      if (!t.L[q]) continue;
+      if (!t.L[q].slices) continue;
       const long long c = chi[q], ct = chi[q + t.delta];
-      all.push_back(problem(abs_(t.L[q]), c, 1, xo(d->off[q]), c, 1, abs_(d->scratch + t.toff[q]), c, (int)ct, (int)c,
-                            (int)c, 0));
+      double* T = d->scratch + t.toff[q];
+      s3.push_back(oz_problem(t.L[q], d->XB[q], T, 0, 0, c, 0));                   // T = L Psi
+      jt.push_back(slice_job(T, 0, 0, c, (int)ct, (int)c, t.T[q]));
+      s4.push_back(oz_problem(t.T[q], t.R[q], nullptr, d->off[q + t.delta], 1, ct, 1));  // Y' += T R^T
     }
-    ED_TRY(close_stage(f));
-    f = all.size();
-    for (int q = 0; q < nq; ++q) {
-      if (!t.L[q]) continue;
-      const long long c = chi[q], ct = chi[q + t.delta];
-      all.push_back(problem(abs_(d->scratch + t.toff[q]), c, 1, abs_(t.R[q]), 1, c, yo(d->off[q + t.delta]), ct,
-                            (int)ct, (int)ct, (int)c, 1));
-    }
-    ED_TRY(close_stage(f));
+    ED_TRY(products(s3));
+    ED_TRY(slices(jt, false));
+    ED_TRY(products(s4));
   }
-  ED_TRY(dense_alloc(d, (void**)&d->d_probs, all.size() * sizeof(GemmProblem)));
-  ED_CUDA_TRY(cudaMemcpy(d->d_probs, all.data(), all.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
   g.d = nullptr;
   *out = d;
   return ED_OK;
@@ -333,8 +245,10 @@ extern "C" ed_status ed_dense_apply(ed_dense* d, const double* x, double* y, voi
   ED_DEVICE_SCOPE(d->device);
   cudaStream_t st = (cudaStream_t)stream;
   for (const auto& s : d->stages) {
-    k_gemm_batch<<<(unsigned)s.tiles, 256, 0, st>>>(d->d_probs + s.first, s.count, x, y);
-    ED_CUDA_TRY(cudaGetLastError());
+    if (s.kind == 2)
+      ED_TRY(oz_gemm(&d->oz, (const OzProblem*)s.list, s.count, s.units, y, st));
+    else
+      ED_TRY(oz_slice(&d->oz, (const OzSliceJob*)s.list, s.count, s.units, s.kind == 1, x, st));
   }
   return ED_OK;
 }

@@ -1,0 +1,465 @@
+// FP64-accurate GEMM on the BF16 tensor cores (Ozaki-style digit
+// splitting, see ozaki.h): digit planes formed on the host or by the slicing
+// kernels here, tiles staged by TMA with 128-byte swizzle, products issued
+// by one thread with tcgen05.mma into FP32 accumulators in TMEM (one per
+// digit order), drained by four warps and combined in FP64.
+#include "ozaki.h"
+
+#include <cmath>
+#include <cstring>
+
+#include "tc.cuh"
+
+namespace edk {
+
+// ---------------------------------------------------------------- digits
+
+// exponent E with maxabs < 2^E (0 for an all-zero row)
+int oz_row_exponent(double maxabs) {
+  if (!(maxabs > 0.0)) return 0;
+  int e;
+  std::frexp(maxabs, &e);  // maxabs = f 2^e, f in [0.5, 1)
+  return e;
+}
+
+// U = round(v 2^(47 - E)) (|U| <= 2^47), then 8 balanced base-64 digits,
+// most significant first: U = sum_p d_p 64^(7 - p), |d_p| <= 32
+void oz_digits_host(double v, int E, int* d) {
+  long long U = std::llrint(std::ldexp(v, kOzFrac - E));
+  for (int p = kOzDigits - 1; p > 0; --p) {
+    const long long r = ((U + 32) & 63) - 32;
+    d[p] = (int)r;
+    U = (U - r) >> kOzBits;
+  }
+  d[0] = (int)U;
+}
+
+__host__ __device__ inline uint16_t bf16_of_small_int(int v) {
+  // |v| <= 32: the BF16 bit pattern of (float)v (8 significant bits suffice)
+  const float f = (float)v;
+  uint32_t u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(f);
+#else
+  std::memcpy(&u, &f, 4);
+#endif
+  return (uint16_t)(u >> 16);
+}
+
+__device__ inline double pow2(int k) {  // 2^k for -1022 <= k <= 1023
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+__device__ inline int exp_of(double maxabs) {  // maxabs < 2^E
+  if (!(maxabs > 0.0)) return 0;
+  const int b = (int)((__double_as_longlong(maxabs) >> 52) & 0x7ff);
+  if (b == 0) return -1021;  // subnormal: below 2^-1022
+  return b - 1022;
+}
+
+__device__ inline void digits_dev(double v, int E, int* d) {
+  long long U = __double2ll_rn(v * pow2(kOzFrac - E));
+#pragma unroll
+  for (int p = kOzDigits - 1; p > 0; --p) {
+    const long long r = ((U + 32) & 63) - 32;
+    d[p] = (int)r;
+    U = (U - r) >> kOzBits;
+  }
+  d[0] = (int)U;
+}
+
+// ---------------------------------------------------------------- context
+
+OzContext::~OzContext() {
+  for (void* p : allocs) cudaFree(p);
+}
+
+ed_status oz_alloc(OzContext* o, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu) for tensor-core operands failed: %s", bytes, cudaGetErrorString(e));
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? ED_ENOMEM : ED_ECUDA;
+  }
+  o->allocs.push_back(*p);
+  return ED_OK;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D map over the digit planes: (K, R, 8) BF16, box (64, box_rows, 1),
+// 128-byte swizzle, out-of-range elements read as zero
+static ed_status make_map(OzContext* o, OzOperand* op, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return ED_ECUDA;
+  }
+  CUtensorMap m;
+  const cuuint64_t dims[3] = {(cuuint64_t)op->K, (cuuint64_t)op->R, (cuuint64_t)kOzDigits};
+  const cuuint64_t strides[2] = {(cuuint64_t)op->Kpad * 2, (cuuint64_t)op->Kpad * 2 * (cuuint64_t)op->R};
+  const cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op->slices, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d operand", (int)r, op->R, op->K);
+    return ED_ECUDA;
+  }
+  op->map = (int)o->maps.size();
+  o->maps.push_back(m);
+  return ED_OK;
+}
+
+static ed_status alloc_operand(OzContext* o, int R, int K, OzOperand* op) {
+  op->R = R;
+  op->K = K;
+  op->Kpad = (K + 7) / 8 * 8;  // 16-byte row stride
+  ED_TRY(oz_alloc(o, (void**)&op->slices, (size_t)kOzDigits * R * op->Kpad * 2));
+  ED_TRY(oz_alloc(o, (void**)&op->exps, (size_t)R * sizeof(int)));
+  return ED_OK;
+}
+
+ed_status oz_operand_host(OzContext* o, const double* h, int R, int K, bool a_role, OzOperand* out) {
+  ED_TRY(alloc_operand(o, R, K, out));
+  const int Kp = out->Kpad;
+  std::vector<uint16_t> s((size_t)kOzDigits * R * Kp, 0);
+  std::vector<int> ex(R);
+  int d[kOzDigits];
+  for (int i = 0; i < R; ++i) {
+    double mx = 0.0;
+    for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(h[(size_t)i * K + k]));
+    const int E = oz_row_exponent(mx);
+    ex[i] = E;
+    for (int k = 0; k < K; ++k) {
+      oz_digits_host(h[(size_t)i * K + k], E, d);
+      for (int p = 0; p < kOzDigits; ++p) s[((size_t)p * R + i) * Kp + k] = bf16_of_small_int(d[p]);
+    }
+  }
+  ED_CUDA_TRY(cudaMemcpy(out->slices, s.data(), s.size() * 2, cudaMemcpyHostToDevice));
+  ED_CUDA_TRY(cudaMemcpy(out->exps, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return make_map(o, out, a_role ? kOzBM : kOzBN);
+}
+
+ed_status oz_operand_device(OzContext* o, int R, int K, bool a_role, OzOperand* out) {
+  ED_TRY(alloc_operand(o, R, K, out));
+  ED_CUDA_TRY(cudaMemset(out->slices, 0, (size_t)kOzDigits * R * out->Kpad * 2));
+  return make_map(o, out, a_role ? kOzBM : kOzBN);
+}
+
+ed_status oz_finish(OzContext* o) {
+  if (o->maps.empty()) return ED_OK;
+  ED_TRY(oz_alloc(o, (void**)&o->d_maps, o->maps.size() * sizeof(CUtensorMap)));
+  ED_CUDA_TRY(cudaMemcpy(o->d_maps, o->maps.data(), o->maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+  if (!o->d_err) {
+    ED_TRY(oz_alloc(o, (void**)&o->d_err, 16));
+    ED_CUDA_TRY(cudaMemset(o->d_err, 0, 16));
+  }
+  return ED_OK;
+}
+
+long long oz_tiles(int M, int N) { return (long long)((M + kOzBM - 1) / kOzBM) * ((N + kOzBN - 1) / kOzBN); }
+
+// ---------------------------------------------------------------- slicing kernels
+
+__device__ inline int find_job(const OzSliceJob* jobs, int n, long long u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].first <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// operand rows = source rows: one warp per row (exponent by a warp max, then
+// the digits of every element, one BF16 plane store per digit)
+__global__ void __launch_bounds__(256) k_oz_slice_rows(const OzSliceJob* __restrict__ jobs, int njobs, long long units,
+                                                       const double* __restrict__ x) {
+  const long long u = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (u >= units) return;
+  const OzSliceJob J = jobs[find_job(jobs, njobs, u)];
+  const int i = (int)(u - J.first);
+  const double* src = (J.sbase == 1 ? x + J.soff : J.src) + (long long)i * J.ld;
+  double mx = 0.0;
+  for (int k = lane; k < J.cols; k += 32) mx = fmax(mx, fabs(src[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int E = exp_of(mx);
+  if (lane == 0) J.exps[i] = E;
+  const long long plane = (long long)J.rows * J.Kpad;
+  uint16_t* row = J.dst + (long long)i * J.Kpad;
+  for (int k = lane; k < J.Kpad; k += 32) {
+    int d[kOzDigits];
+    digits_dev(k < J.cols ? src[k] : 0.0, E, d);
+#pragma unroll
+    for (int p = 0; p < kOzDigits; ++p) row[p * plane + k] = bf16_of_small_int(d[p]);
+  }
+}
+
+// operand rows = source columns (the transpose): one CTA per strip of 32
+// source columns -- per-column exponent over all rows, then 32 x 32 tiles
+// transposed through shared memory so both reads and digit stores coalesce
+__global__ void __launch_bounds__(256) k_oz_slice_cols(const OzSliceJob* __restrict__ jobs, int njobs,
+                                                       long long units, const double* __restrict__ x) {
+  __shared__ double tile[32][33];
+  __shared__ double cmax[8][32];
+  __shared__ int cexp[32];
+  const long long u = blockIdx.x;
+  if (u >= units) return;
+  const OzSliceJob J = jobs[find_job(jobs, njobs, u)];
+  const int c0 = (int)(u - J.first) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double* src = J.sbase == 1 ? x + J.soff : J.src;
+  double mx = 0.0;
+  if (c0 + tx < J.cols)
+    for (int r = ty; r < J.rows; r += 8) mx = fmax(mx, fabs(src[(long long)r * J.ld + c0 + tx]));
+  cmax[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    double m = 0.0;
+    for (int q = 0; q < 8; ++q) m = fmax(m, cmax[q][tx]);
+    const int E = exp_of(m);
+    cexp[tx] = E;
+    if (c0 + tx < J.cols) J.exps[c0 + tx] = E;
+  }
+  __syncthreads();
+  const long long plane = (long long)J.cols * J.Kpad;  // operand rows = source columns
+  for (int r0 = 0; r0 < J.Kpad; r0 += 32) {
+    for (int q = ty; q < 32; q += 8) {
+      const int r = r0 + q, c = c0 + tx;
+      tile[q][tx] = (r < J.rows && c < J.cols) ? src[(long long)r * J.ld + c] : 0.0;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+      const int c = c0 + q, k = r0 + tx;  // operand row c, column k
+      if (c < J.cols && k < J.Kpad) {
+        int d[kOzDigits];
+        digits_dev(tile[tx][q], cexp[q], d);
+        uint16_t* row = J.dst + (long long)c * J.Kpad;
+#pragma unroll
+        for (int p = 0; p < kOzDigits; ++p) row[p * plane + k] = bf16_of_small_int(d[p]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+ed_status oz_slice(OzContext* o, const OzSliceJob* d_jobs, int njobs, long long units, bool transpose,
+                   const double* x, cudaStream_t st) {
+  if (units <= 0) return ED_OK;
+  if (transpose)
+    k_oz_slice_cols<<<(unsigned)units, 256, 0, st>>>(d_jobs, njobs, units, x);
+  else
+    k_oz_slice_rows<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(d_jobs, njobs, units, x);
+  ED_CUDA_TRY(cudaGetLastError());
+  return ED_OK;
+}
+
+// ---------------------------------------------------------------- the GEMM
+
+constexpr int kOzThreads = 192;          // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
+constexpr int kOzAStages = 3;
+constexpr int kOzATile = kOzBM * kOzBK * 2;   // 16 KB
+constexpr int kOzBTile = kOzBN * kOzBK * 2;   // 8 KB
+constexpr int kOzBBuf = kOzDigits * kOzBTile; // the 8 digit planes of one K step: 64 KB
+constexpr int kOzTmemCols = 512;              // 8 accumulators of 64 columns
+constexpr long long kOzSpin = 1ll << 26;      // bounded waits (about a second)
+constexpr size_t kOzSmem = 1024 + 2 * kOzBBuf + kOzAStages * kOzATile + 256;
+
+__device__ inline int find_prob(const OzProblem* probs, int n, long long tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+    k_oz_gemm(const OzProblem* __restrict__ probs, int nprob, const CUtensorMap* __restrict__ maps, double* y,
+              int* err) {
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = sm;                       // [2][8 planes][64 rows][128 B]
+  unsigned char* sA = sm + 2 * kOzBBuf;         // [3][128 rows][128 B]
+  uint64_t* bar = (uint64_t*)(sA + kOzAStages * kOzATile);
+  uint64_t* b_full = bar;          // 2
+  uint64_t* b_empty = bar + 2;     // 2
+  uint64_t* a_full = bar + 4;      // 3
+  uint64_t* a_empty = bar + 7;     // 3
+  uint64_t* acc_full = bar + 10;
+  uint64_t* acc_empty = bar + 11;
+  uint64_t* mma_done = bar + 12;
+  __shared__ unsigned s_tmem;
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const OzProblem P = probs[find_prob(probs, nprob, (long long)blockIdx.x)];
+  const long long t = (long long)blockIdx.x - P.tile0;
+  const int m0 = (int)(t / P.tiles_n) * kOzBM, n0 = (int)(t % P.tiles_n) * kOzBN;
+  const int nkb = (P.K + kOzBK - 1) / kOzBK;
+  const int kb_per_chunk = kOzKChunk / kOzBK;
+  const int nchunk = (nkb + kb_per_chunk - 1) / kb_per_chunk;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&b_full[i], 1);
+      tc::mbar_init(&b_empty[i], 1);
+    }
+    for (int i = 0; i < kOzAStages; ++i) {
+      tc::mbar_init(&a_full[i], 1);
+      tc::mbar_init(&a_empty[i], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, 128);
+    tc::mbar_init(mma_done, 1);
+    tc::fence_mbar_init();
+    s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&s_tmem, kOzTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const unsigned tmem = s_tmem;
+
+  if (warp == 4) {
+    // ---- TMA producer: per K step the 8 digit planes of B^T, then A's planes one by one
+    if (lane == 0) {
+      const CUtensorMap* ma = maps + P.mapA;
+      const CUtensorMap* mb = maps + P.mapB;
+      long long na = 0;
+      for (int kb = 0; kb < nkb && !s_abort; ++kb) {
+        const int b = kb & 1, ub = kb >> 1;
+        if (ub > 0 && !tc::mbar_wait(&b_empty[b], (ub - 1) & 1, kOzSpin)) { s_abort = 1; break; }
+        tc::mbar_expect_tx(&b_full[b], kOzBBuf);
+        for (int q = 0; q < kOzDigits; ++q)
+          tc::tma_load_3d(sB + b * kOzBBuf + q * kOzBTile, mb, kb * kOzBK, n0, q, &b_full[b]);
+        for (int p = 0; p < kOzDigits; ++p, ++na) {
+          const int s = (int)(na % kOzAStages);
+          const long long ua = na / kOzAStages;
+          if (ua > 0 && !tc::mbar_wait(&a_empty[s], (unsigned)((ua - 1) & 1), kOzSpin)) { s_abort = 1; break; }
+          tc::mbar_expect_tx(&a_full[s], kOzATile);
+          tc::tma_load_3d(sA + s * kOzATile, ma, kb * kOzBK, m0, p, &a_full[s]);
+        }
+      }
+      if (s_abort) atomicExch(err, 1);
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer: accumulator g (TMEM columns 64 g) sums the digit pairs p + q = g
+    if (lane == 0) {
+      const unsigned idesc = tc::idesc_bf16_f32(kOzBM, kOzBN);
+      long long na = 0;
+      for (int c = 0; c < nchunk && !s_abort; ++c) {
+        if (c > 0 && !tc::mbar_wait(acc_empty, (c - 1) & 1, kOzSpin)) { s_abort = 1; break; }
+        tc::tc_fence_after();
+        const int kb_end = min(nkb, (c + 1) * kb_per_chunk);
+        for (int kb = c * kb_per_chunk; kb < kb_end && !s_abort; ++kb) {
+          const int b = kb & 1, ub = kb >> 1;
+          if (!tc::mbar_wait(&b_full[b], ub & 1, kOzSpin)) { s_abort = 1; break; }
+          tc::tc_fence_after();
+          const bool first_kb = kb == c * kb_per_chunk;
+          for (int p = 0; p < kOzDigits; ++p, ++na) {
+            const int s = (int)(na % kOzAStages);
+            if (!tc::mbar_wait(&a_full[s], (unsigned)((na / kOzAStages) & 1), kOzSpin)) { s_abort = 1; break; }
+            tc::tc_fence_after();
+            const uint64_t da = tc::sdesc_kmajor_sw128(sA + s * kOzATile);
+            for (int q = 0; q + p < kOzDigits; ++q) {
+              const uint64_t db = tc::sdesc_kmajor_sw128(sB + b * kOzBBuf + q * kOzBTile);
+              const unsigned dt = tmem + (unsigned)((p + q) * kOzBN);
+#pragma unroll
+              for (int kk = 0; kk < kOzBK / 16; ++kk)  // 32 bytes of K per instruction
+                tc::mma_bf16(dt, da + 2 * kk, db + 2 * kk, idesc, !(first_kb && p == 0 && kk == 0));
+            }
+            tc::mma_commit(&a_empty[s]);
+          }
+          tc::mma_commit(&b_empty[b]);
+        }
+        tc::mma_commit(acc_full);
+      }
+      // every issued MMA finishes before the accumulators are released
+      tc::mma_commit(mma_done);
+      if (!tc::mbar_wait(mma_done, 0, kOzSpin)) s_abort = 1;
+      if (s_abort) atomicExch(err, 1);
+    }
+  } else {
+    // ---- epilogue: thread = one output row, 64 columns in FP64
+    const int row = warp * 32 + lane;
+    double acc[kOzBN];
+#pragma unroll
+    for (int j = 0; j < kOzBN; ++j) acc[j] = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      bool ok = false;
+      for (long long i = 0; i < kOzSpin && !ok; ++i) {
+        ok = tc::mbar_try(acc_full, c & 1);
+        if (!ok && s_abort) break;
+      }
+      if (!ok) { s_abort = 1; break; }
+      tc::tc_fence_after();
+#pragma unroll
+      for (int g = 0; g < kOzDigits; ++g) {
+        const double sc = pow2(-kOzBits * g);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(g * kOzBN + 32 * h), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[32 * h + j] = fma((double)v[j], sc, acc[32 * h + j]);
+        }
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(acc_empty);
+    }
+    const int i = m0 + row;
+    if (!s_abort && i < P.M) {
+      const int ea = P.ea[i];
+      double* crow = (P.cbase == 1 ? y + P.coff : P.C) + (long long)i * P.ldc;
+#pragma unroll
+      for (int j = 0; j < kOzBN; ++j) {
+        const int col = n0 + j;
+        if (col < P.N) {
+          const double v = acc[j] * pow2(ea + P.eb[col] - 10);
+          crow[col] = P.acc ? crow[col] + v : v;
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kOzTmemCols);
+  }
+}
+
+ed_status oz_gemm(OzContext* o, const OzProblem* d_probs, int nprob, long long tiles, double* y, cudaStream_t st) {
+  if (tiles <= 0) return ED_OK;
+  static bool attr = false;
+  if (!attr) {
+    ED_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem));
+    attr = true;
+  }
+  k_oz_gemm<<<(unsigned)tiles, kOzThreads, kOzSmem, st>>>(d_probs, nprob, o->d_maps, y, o->d_err);
+  ED_CUDA_TRY(cudaGetLastError());
+  return ED_OK;
+}
+
+}  // namespace edk
