@@ -217,8 +217,11 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  *   entropy  host (nullable): -sum p ln p over p = lambda / sum(weight) > 0
  *   stage_ms host (nullable), 2 doubles: device time of the Gram kernels and
  *            of the eigensolver, summed over the blocks (CUDA events)
- * Device memory: one Gram matrix of the largest block (8 min(dA,dB)^2
- * bytes) plus the eigensolver workspace; blocks with min(dA,dB) > 46340 are
+ * The Gram matrices are formed on the tensor cores in FP64-accurate
+ * digit-split form (8 BF16 digit planes per value, exact FP32 sums per digit
+ * order, FP64 combination).  Device memory: one Gram matrix of the largest
+ * block (8 min(dA,dB)^2 bytes), the digit planes of one block (16 bytes per
+ * element) and the eigensolver workspace; blocks with min(dA,dB) > 46340 are
  * ED_EUNSUPPORTED.  Synchronises the stream. */
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
                                    double* weight, double* entropy, double* stage_ms, void* stream);
@@ -230,8 +233,12 @@ ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambd
  * row-major blocks Psi_q (dimension sum_q chi_q^2), and
  *   (H psi)_q' = H_L,q' Psi_q' + Psi_q' H_R,q'^T + sum_m L_m,q Psi_q R_m,q^T
  * over the cross terms m with q' = q + delta[m] (the Vec identity
- * [L (x) R] Vec(Psi) = Vec(L Psi R^T), row-major).  Every product runs in
- * this library's FP64 batched GEMM kernel, one launch per stage.
+ * [L (x) R] Vec(Psi) = Vec(L Psi R^T), row-major).  Every product runs on
+ * the tensor cores in FP64-accurate digit-split form (each FP64 row scaled
+ * by a power of two and split into 8 BF16 digits; digit products summed
+ * exactly in FP32 per digit order, combined in FP64), one launch per stage.
+ * A tensor-core wait that runs out (it should not) sets an error flag the
+ * library keeps, and the apply's output is then incomplete.
  *   HL, HR   host pointers, one per block: chi_q x chi_q row-major
  *   delta    per cross term, nonzero
  *   Lm, Rm   host pointers [m * nq + q]: chi_{q+delta} x chi_q row-major for

@@ -66,6 +66,7 @@ OzProblem oz_problem(const OzOperand& A, const OzOperand& B, double* C, long lon
   p.K = A.K;
   p.acc = acc;
   p.tiles_n = (B.R + kOzBN - 1) / kOzBN;
+  p.tri = 0;
   p.tile0 = 0;
   return p;
 }

@@ -6,11 +6,12 @@
 // In the block layout rho_A is block diagonal, rho_A(s) = Psi_s Psi_s^T, and
 // its nonzero eigenvalues are those of the Gram matrix of Psi_s in the
 // smaller of its two dimensions (the squared singular values of Psi_s).
-// k_gram forms that Gram matrix in FP64 (one 64 x 64 output tile per CTA,
-// upper-triangle tiles only: the matrix is symmetric); the eigenvalues of
-// each Gram matrix come from cuSOLVER's dense symmetric divide-and-conquer
-// eigensolver, which is loaded with dlopen on the first call so that the
-// rest of the library does not depend on it.
+// The Gram matrix is formed on the tensor cores by the FP64-accurate
+// digit-split GEMM (ozaki.cu; one digit-plane buffer serves as both factors,
+// only the tiles on or below the diagonal are computed: the matrix is
+// symmetric); the eigenvalues of each Gram matrix come from cuSOLVER's dense
+// symmetric divide-and-conquer eigensolver, which is loaded with dlopen on
+// the first call so that the rest of the library does not depend on it.
 #include <dlfcn.h>
 
 #include <cmath>
@@ -19,67 +20,10 @@
 #include <cusolverDn.h>
 
 #include "krylov.h"
+#include "ozaki.h"
 
 namespace edk {
 namespace {
-
-constexpr int kGT = 64;  // output tile (rows and columns)
-constexpr int kGK = 16;  // contraction depth staged per step
-
-// G[i][j] = sum_l X(i,l) X(j,l) over the tiles (ti, tj) with ti <= tj, with
-// X(i,l) = x[i*si + l*sl], 0 <= i < m, 0 <= l < L; G row-major, leading
-// dimension m.  Its row-major upper triangle is the column-major lower
-// triangle that the eigensolver reads.
-__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ x, long long si, long long sl, int m,
-                                              long long L, double* __restrict__ G, int T) {
-  __shared__ double As[kGK][kGT + 1];
-  __shared__ double Bs[kGK][kGT + 1];
-  int t = blockIdx.x, ti = 0;
-  while (t >= T - ti) {
-    t -= T - ti;
-    ++ti;
-  }
-  const int tj = ti + t;
-  const long long i0 = (long long)ti * kGT, j0 = (long long)tj * kGT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const bool lfast = sl == 1;  // the contraction index is the contiguous one
-  double acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
-  for (long long l0 = 0; l0 < L; l0 += kGK) {
-    for (int e = threadIdx.x; e < kGT * kGK; e += blockDim.x) {
-      const int r = lfast ? e / kGK : e % kGT;
-      const int l = lfast ? e % kGK : e / kGT;
-      const long long gl = l0 + l, gi = i0 + r, gj = j0 + r;
-      As[l][r] = (gi < m && gl < L) ? x[gi * si + gl * sl] : 0.0;
-      Bs[l][r] = (gj < m && gl < L) ? x[gj * si + gl * sl] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kGK; ++k) {
-      double a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = As[k][ty + 16 * u];
-        b[u] = Bs[k][tx + 16 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const long long i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
-      if (i < m && j < m) G[i * m + j] = acc[u][v];
-    }
-}
 
 // the five cuSOLVER entry points used here, resolved once
 struct Solver {
@@ -208,12 +152,69 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
   ED_TRY(mem.get((void**)&W, (size_t)mmax * sizeof(double)));
   ED_TRY(mem.get((void**)&info, sizeof(int)));
   int lwork = 0;
-  if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, (int)mmax, G, (int)mmax, W, &lwork) !=
+  if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_UPPER, (int)mmax, G, (int)mmax, W, &lwork) !=
       CUSOLVER_STATUS_SUCCESS) {
     set_error("cuSOLVER workspace query failed");
     return ED_ECUDA;
   }
   ED_TRY(mem.get((void**)&work, (size_t)std::max(lwork, 1) * sizeof(double)));
+
+  // digit planes of one block at a time (both factors of its Gram matrix),
+  // tensor maps and launch lists of every block built up front
+  OzContext oz;
+  oz.device = c->device;
+  OzOperand X;
+  long long max_elems = 1;
+  for (const Block& b : c->blocks) {
+    const long long m = std::min(b.dA, b.dB), L = std::max(b.dA, b.dB);
+    max_elems = std::max(max_elems, m * ((L + 7) / 8 * 8));
+  }
+  ED_TRY(oz_operand_buffer(&oz, max_elems, mmax, &X));
+  std::vector<OzSliceJob> jobs;
+  std::vector<OzProblem> probs;
+  std::vector<long long> units, tiles;
+  for (const Block& b : c->blocks) {
+    const int m = (int)std::min(b.dA, b.dB), L = (int)std::max(b.dA, b.dB);
+    int ma = 0, mb = 0;
+    ED_TRY(oz_map(&oz, &X, m, L, true, &ma));
+    ED_TRY(oz_map(&oz, &X, m, L, false, &mb));
+    OzSliceJob j{};
+    j.src = psi + b.off;
+    j.sbase = 0;
+    j.ld = b.dB;
+    j.rows = (int)b.dA;
+    j.cols = (int)b.dB;
+    j.dst = X.slices;
+    j.exps = X.exps;
+    j.Kpad = (L + 7) / 8 * 8;
+    j.first = 0;
+    jobs.push_back(j);
+    // Psi Psi^T (rows, dA <= dB) or Psi^T Psi (columns)
+    units.push_back(b.dA <= b.dB ? (long long)b.dA : (b.dB + 31) / 32);
+    OzProblem p{};
+    p.mapA = ma;
+    p.mapB = mb;
+    p.ea = X.exps;
+    p.eb = X.exps;
+    p.C = G;
+    p.cbase = 0;
+    p.ldc = m;
+    p.M = p.N = m;
+    p.K = L;
+    p.acc = 0;
+    p.tiles_n = (m + kOzBN - 1) / kOzBN;
+    p.tri = 1;
+    p.tile0 = 0;
+    probs.push_back(p);
+    tiles.push_back(oz_tiles(m, m, 1));
+  }
+  ED_TRY(oz_finish(&oz));
+  OzSliceJob* d_jobs = nullptr;
+  OzProblem* d_probs = nullptr;
+  ED_TRY(oz_alloc(&oz, (void**)&d_jobs, jobs.size() * sizeof(OzSliceJob)));
+  ED_TRY(oz_alloc(&oz, (void**)&d_probs, probs.size() * sizeof(OzProblem)));
+  ED_CUDA_TRY(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(OzSliceJob), cudaMemcpyHostToDevice));
+  ED_CUDA_TRY(cudaMemcpy(d_probs, probs.data(), probs.size() * sizeof(OzProblem), cudaMemcpyHostToDevice));
 
   std::vector<double> w(mmax);
   std::vector<double> wt(c->blocks.size());
@@ -226,22 +227,18 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     const double* xb = psi + b.off;
     const int m = (int)std::min(b.dA, b.dB);
     // Gram matrix in the smaller dimension: Psi Psi^T (rows) or Psi^T Psi (columns)
-    const bool rows = b.dA <= b.dB;
-    const long long si = rows ? b.dB : 1, sl = rows ? 1 : b.dB, L = rows ? b.dB : b.dA;
-    const int T = (m + kGT - 1) / kGT;
-    const long long tiles = (long long)T * (T + 1) / 2;
     ED_CUDA_TRY(cudaEventRecord(ev.e[0], st));
-    k_gram<<<(unsigned)tiles, 256, 0, st>>>(xb, si, sl, m, L, G, T);
-    ED_CUDA_TRY(cudaGetLastError());
+    ED_TRY(oz_slice(&oz, d_jobs + bi, 1, units[bi], b.dA > b.dB, nullptr, st));
+    ED_TRY(oz_gemm(&oz, d_probs + bi, 1, tiles[bi], nullptr, st));
     ED_CUDA_TRY(cudaEventRecord(ev.e[1], st));
     int lw = 0;
-    if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, G, m, W, &lw) !=
+    if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_UPPER, m, G, m, W, &lw) !=
             CUSOLVER_STATUS_SUCCESS ||
         lw > lwork) {
       set_error("cuSOLVER workspace for dimension %d exceeds the one allocated", m);
       return ED_ECUDA;
     }
-    if (S.syevd(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, G, m, W, work, lwork, info) !=
+    if (S.syevd(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_UPPER, m, G, m, W, work, lwork, info) !=
         CUSOLVER_STATUS_SUCCESS) {
       set_error("cuSOLVER eigensolver failed on block %zu (dimension %d)", bi, m);
       return ED_ECUDA;

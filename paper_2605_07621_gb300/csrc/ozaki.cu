@@ -176,7 +176,29 @@ ed_status oz_finish(OzContext* o) {
   return ED_OK;
 }
 
-long long oz_tiles(int M, int N) { return (long long)((M + kOzBM - 1) / kOzBM) * ((N + kOzBN - 1) / kOzBN); }
+// tile rows of a triangular problem hold min(tiles_n, 2 (tm + 1)) tiles (BM = 2 BN)
+long long oz_tiles(int M, int N, int tri) {
+  const long long tm = (M + kOzBM - 1) / kOzBM, tn = (N + kOzBN - 1) / kOzBN;
+  if (!tri) return tm * tn;
+  long long t = 0;
+  for (long long i = 0; i < tm; ++i) t += std::min(tn, 2 * (i + 1));
+  return t;
+}
+
+ed_status oz_operand_buffer(OzContext* o, long long max_elems, long long max_rows, OzOperand* out) {
+  ED_TRY(oz_alloc(o, (void**)&out->slices, (size_t)kOzDigits * (size_t)max_elems * 2));
+  ED_TRY(oz_alloc(o, (void**)&out->exps, (size_t)max_rows * sizeof(int)));
+  return ED_OK;
+}
+
+ed_status oz_map(OzContext* o, OzOperand* op, int R, int K, bool a_role, int* map) {
+  op->R = R;
+  op->K = K;
+  op->Kpad = (K + 7) / 8 * 8;
+  ED_TRY(make_map(o, op, a_role ? kOzBM : kOzBN));
+  *map = op->map;
+  return ED_OK;
+}
 
 // ---------------------------------------------------------------- slicing kernels
 
@@ -314,8 +336,20 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const OzProblem P = probs[find_prob(probs, nprob, (long long)blockIdx.x)];
-  const long long t = (long long)blockIdx.x - P.tile0;
-  const int m0 = (int)(t / P.tiles_n) * kOzBM, n0 = (int)(t % P.tiles_n) * kOzBN;
+  long long t = (long long)blockIdx.x - P.tile0;
+  int m0, n0;
+  if (!P.tri) {
+    m0 = (int)(t / P.tiles_n) * kOzBM;
+    n0 = (int)(t % P.tiles_n) * kOzBN;
+  } else {  // tile row tm holds the column tiles 0 .. min(tiles_n, 2 tm + 2) - 1
+    int tm = 0;
+    while (t >= min((long long)P.tiles_n, 2ll * (tm + 1))) {
+      t -= min((long long)P.tiles_n, 2ll * (tm + 1));
+      ++tm;
+    }
+    m0 = tm * kOzBM;
+    n0 = (int)t * kOzBN;
+  }
   const int nkb = (P.K + kOzBK - 1) / kOzBK;
   const int kb_per_chunk = kOzKChunk / kOzBK;
   const int nchunk = (nkb + kb_per_chunk - 1) / kb_per_chunk;

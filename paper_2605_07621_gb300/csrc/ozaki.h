@@ -48,6 +48,7 @@ struct OzProblem {
   long long ldc;
   int M, N, K, acc;
   int tiles_n;
+  int tri;             // 1: only the tiles on or below the diagonal (C symmetric, its lower triangle)
   long long tile0;
 };
 
@@ -67,6 +68,10 @@ ed_status oz_operand_host(OzContext* o, const double* h, int R, int K, bool a_ro
 // operand buffers filled on the device by oz_slice_* (no data yet)
 ed_status oz_operand_device(OzContext* o, int R, int K, bool a_role, OzOperand* out);
 ed_status oz_finish(OzContext* o);  // upload the tensor maps
+// operand buffers for up to R x K (no map); a map over its first R rows and K
+// columns (digit planes of an R x K operand with row stride Kpad)
+ed_status oz_operand_buffer(OzContext* o, long long max_elems, long long max_rows, OzOperand* out);
+ed_status oz_map(OzContext* o, OzOperand* op, int R, int K, bool a_role, int* map);
 
 // digit planes of matrices on the device (FP64, row-major, leading dimension
 // ld), one job per matrix; rows: the matrix rows become the operand's rows;
@@ -85,7 +90,7 @@ struct OzSliceJob {
 ed_status oz_slice(OzContext* o, const OzSliceJob* d_jobs, int njobs, long long units, bool transpose,
                    const double* x, cudaStream_t st);
 ed_status oz_gemm(OzContext* o, const OzProblem* d_probs, int nprob, long long tiles, double* y, cudaStream_t st);
-long long oz_tiles(int M, int N);
+long long oz_tiles(int M, int N, int tri = 0);
 // host-side digit planes (for tests and static operands): U and digits of v
 void oz_digits_host(double v, int E, int* d);
 int oz_row_exponent(double maxabs);
