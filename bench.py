@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--batch-n", type=int, default=512)
     p.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrival rate (requests/s)")
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
+    p.add_argument("--dense-only", action="store_true",
+                   help="run only the dense-block (digit-split tensor-core) measurement and print it")
     p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
     p.add_argument("--no-entangle", action="store_true", help="skip the entanglement spectrum of the ground state")
     p.add_argument("--no-dense", action="store_true", help="skip the dense-block (DMRG-style) H psi")
@@ -91,10 +93,23 @@ def sum_over_ranks(value: float, world: int, device: str = "cpu") -> float:
     return float(t.item())
 
 
-# FP64 peak of this GPU: the nominal dense figure, 1.25 TFLOP/s.  The own
-# pipe microbenchmark (`bench.py --pipes`) reads 0.505 T FMA/s = 1.01 TFLOP/s,
-# which the Gram kernel exceeds, so the nominal figure is the denominator.
-FP64_TFLOPS_NOMINAL = 1.25
+# Digit-split tensor-core GEMM (the dense-block products and the Gram
+# matrices): each FP64 product runs as 36 BF16 digit-pair products (digit
+# orders p + q <= 7 of 8 digits) on 128 x 64 output tiles with K in steps of
+# 64; the BF16 FLOPs it executes are counted on those padded tiles.
+OZ_PAIRS = 36
+
+
+def oz_tensor_flops(M, N, K, tri=False):
+    """BF16 FLOPs the tensor cores execute for one digit-split product."""
+    tm, tn, tk = -(-M // 128), -(-N // 64), -(-K // 64)
+    tiles = sum(min(tn, 2 * (i + 1)) for i in range(tm)) if tri else tm * tn
+    return 2.0 * tiles * 128 * 64 * tk * 64 * OZ_PAIRS
+
+
+def bf16_peak():
+    peaks, src = measured_peaks()
+    return float(peaks.get("bf16_tflops", 1900.0)), src
 
 
 def entanglement_section(ed, ctx):
@@ -117,17 +132,21 @@ def entanglement_section(ed, ctx):
     m = np.minimum(dA, dB).astype(np.float64)
     L = np.maximum(dA, dB).astype(np.float64)
     macs = float(np.sum(m * (m + 1) / 2 * L))  # lower triangle with the diagonal
+    tflops = sum(oz_tensor_flops(int(a), int(a), int(b), tri=True) for a, b in zip(m, L))
     gram_ms, eig_ms = es.stage_ms
     tot = float(es.weight.sum())
     W = es.weight / tot
     w_dim = (dA * dB) / float(np.sum(dA * dB))
     xi_low = [float(-np.log(l[0] / tot)) if len(l) and l[0] > 0 else None for l in es.lam]
-    achieved = 2 * macs / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
-    peak = FP64_TFLOPS_NOMINAL
+    peak, src = bf16_peak()
+    achieved = tflops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
     return {"ground_state_s": t_gs, "e0": r.e0, "seconds": t_es, "gram_ms": gram_ms, "eigensolver_ms": eig_ms,
-            "gram_roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                              "frac": achieved / peak if achieved else None, "flops": 2 * macs,
-                              "peak_source": "nominal FP64 dense (no measured FP64 peak in MEASURED_PEAKS.json)"},
+            "gram_fp64_equiv_tflops": 2 * macs / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None,
+            "gram_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                              "frac": achieved / peak if achieved else None, "flops": tflops,
+                              "peak_source": f"{src} BF16 (burst)",
+                              "note": "BF16 FLOPs executed by the digit-split products (36 digit pairs, padded "
+                                      "tiles, triangular tile set)"},
             "entropy": es.entropy, "s": [int(v) for v in s], "W_q": [float(v) for v in W],
             "xi_lowest_per_sector": xi_low, "n_eff_weights": float(1.0 / np.sum(W ** 2)),
             "n_eff_dims": float(1.0 / np.sum(w_dim ** 2)), "levels": int(sum(len(l) for l in es.lam))}
@@ -143,17 +162,21 @@ def dense_blocks_section(ed):
     import workloads.dense as WD
 
     out = {}
+    peak, src = bf16_peak()
     for alpha in (0.95, 0.15, 1.11):
         m = WD.dense_config(alpha)
         op = ed.DenseOperator(m)
-        flops = 0.0
-        for c in m.chi.astype(np.float64):
-            flops += 4.0 * c ** 3
+        flops = 0.0   # FP64-equivalent (2 M N K per product)
+        tflops = 0.0  # BF16 FLOPs the tensor cores execute
+        for c in m.chi.astype(np.int64):
+            flops += 4.0 * float(c) ** 3
+            tflops += 2 * oz_tensor_flops(int(c), int(c), int(c))
         for d, Ls in zip(m.delta, m.Lm):
             for q, l in enumerate(Ls):
                 if l is not None:
                     ct, c = l.shape
                     flops += 2.0 * ct * c * c + 2.0 * ct * ct * c
+                    tflops += oz_tensor_flops(ct, c, c) + oz_tensor_flops(ct, ct, c)
         rng = np.random.default_rng(3)
         x = rng.standard_normal(m.dim)
         xd = torch.tensor(x, device="cuda")
@@ -168,10 +191,12 @@ def dense_blocks_section(ed):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 5
-        tf = flops / (ms * 1e-3) / 1e12
+        ach = tflops / (ms * 1e-3) / 1e12
         out[f"alpha_{alpha}"] = {"chi_max": int(m.chi.max()), "sum_chi": int(m.chi.sum()), "states": m.dim,
-                                 "ms": ms, "tflops": tf, "frac_fp64_peak": tf / FP64_TFLOPS_NOMINAL,
-                                 "flops": flops}
+                                 "ms": ms, "fp64_equiv_tflops": flops / (ms * 1e-3) / 1e12, "fp64_flops": flops,
+                                 "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                              "frac": ach / peak, "flops": tflops,
+                                              "peak_source": f"{src} BF16 (burst)"}}
         op.close()
         del xd, yd
     return out
@@ -467,6 +492,11 @@ def main():
         return run_reference(args)
     import torch
 
+    if args.dense_only:
+        import paper_2605_07621_gb300 as ed
+
+        print(json.dumps(dense_blocks_section(ed)), flush=True)
+        return
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
@@ -542,15 +572,18 @@ def main():
     peaks, peak_src = measured_peaks()
     alg_bytes = 2 * D * esz
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
-    traffic = None
+    traffic = whole_traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         ent = tr.get(f"{args.config}:{args.dtype}")
         if ent and ent.get("kernel_hash") == kernel_source_hash():
             traffic = ent["dram_bytes_per_launch"]
+        ent = tr.get(f"{args.config}:{args.dtype}:whole_apply")
+        if ent and ent.get("kernel_hash") == kernel_source_hash():
+            whole_traffic = ent["dram_bytes_per_apply"]
     except Exception:
-        traffic = None
+        traffic = whole_traffic = None
     # dominant kernel: the row pass (stage 2) -- reads every row of x once and
     # writes every element of y once, i.e. the algorithmic bytes of H|psi>
     names = ["k_exp_max", "k_to_fixed", ctx.row_pass(tdt), "k_panel4"]
@@ -562,7 +595,9 @@ def main():
             "peak_source": peak_src, "kernel": names[dom], "kernel_ms": dom_ms,
             "algorithmic_bytes_per_launch": alg_bytes,
             "stage_ms": {n: float(v) for n, v in zip(names, stage_ms)},
-            "whole_apply": {"achieved": achieved, "frac": achieved / peaks["hbm_gbs"], "ms": ms_per_step}}
+            "whole_apply": {"achieved": achieved, "frac": achieved / peaks["hbm_gbs"], "ms": ms_per_step,
+                            "traffic": whole_traffic,
+                            "traffic_vs_algorithmic": (whole_traffic / alg_bytes) if whole_traffic else None}}
 
     # end to end through the C ABI with host buffers: H2D x, H psi, D2H y
     e2e = None
