@@ -64,7 +64,7 @@ constexpr bool kListsF32 = false;
 template <class Pol, int R, int NT = kRowThreads, int MINB = 2>
 __global__ void __launch_bounds__(NT, MINB)
     k_row5(P3 p, const long long* __restrict__ grp_start, long long n_groups, const typename Pol::S* __restrict__ x,
-           typename Pol::S* __restrict__ y, const int* __restrict__ emax, long long stage_elems, int* err) {
+           typename Pol::Y* __restrict__ y, const int* __restrict__ emax, long long stage_elems, int* err) {
   using S = typename Pol::S;
   extern __shared__ __align__(16) unsigned char smem5[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem5);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(NT, MINB)
     phase ^= 1;
     unsigned pa[R];
     const S* xs[R];
-    S da[R];
+    typename Pol::D da[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int rr = r < nr ? r : 0;
@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(NT, MINB)
       const long long gB = gB0 + b;
       const uint2 m = t.B_meta4[gB];
       const unsigned pb = t.B_pack[gB];
-      const S dbv = Pol::diagB(t, gB);
-      S acc[R];
+      const typename Pol::D dbv = Pol::diagB(t, gB);
+      typename Pol::Y acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const unsigned z = t.vab_and ? (pa[r] & pb) : (pa[r] ^ pb);
-        acc[r] = (da[r] + dbv + Pol::vab(t, z)) * xs[r][b];
+        acc[r] = Pol::dmul(da[r] + dbv + Pol::vab(t, z), xs[r][b]);
       }
       const uint2* cp = t.B_col4 + m.x;
       // index groups in flight per class step (measured best: 4 for 8-byte
@@ -241,9 +241,9 @@ __global__ void __launch_bounds__(NT, MINB)
           }
         }
         cp += n4;
-        const S wc = Pol::w(t, c);
+        const typename Pol::W wc = Pol::w(t, c);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += wc * sum[r];
+        for (int r = 0; r < R; ++r) acc[r] += Pol::wmul(wc, sum[r]);
       }
       if (p.ncross) {
         unsigned dr[R];
@@ -289,9 +289,9 @@ __global__ void __launch_bounds__(NT, MINB)
               }
           }
           {
-            const S w0 = Pol::w(t, t.xl_c[0]), w1 = Pol::w(t, t.xl_c[1]);
+            const typename Pol::W w0 = Pol::w(t, t.xl_c[0]), w1 = Pol::w(t, t.xl_c[1]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] += w0 * s0[r] + w1 * s1[r];
+            for (int r = 0; r < R; ++r) acc[r] += Pol::wmul(w0, s0[r]) + Pol::wmul(w1, s1[r]);
           }
         } else if constexpr (sizeof(S) == 4) {
           // 4-byte types (four rows per pass): loop over every bond with
@@ -305,12 +305,12 @@ __global__ void __launch_bounds__(NT, MINB)
             while (km) {
               const int k = __ffs(km) - 1;
               km &= km - 1;
-              const S wk = Pol::bw(t, k);
+              const typename Pol::W wk = Pol::bw(t, k);
               const int ia = t.bond_ia[k];
 #pragma unroll
               for (int r = 0; r < R; ++r) {
                 const S* sp = src_row[r][ia];
-                if (((dr[r] >> k) & 1u) && sp) acc[r] += wk * __ldg(sp + mq);
+                if (((dr[r] >> k) & 1u) && sp) acc[r] += Pol::wmul(wk, __ldg(sp + mq));
               }
             }
           }
@@ -345,9 +345,9 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
             for (int q = 0; q < kXB; ++q)
               if (kq[q] >= 0) {
-                const S w = Pol::bw(t, kq[q]);
+                const typename Pol::W w = Pol::bw(t, kq[q]);
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += w * v[r][q];
+                for (int r = 0; r < R; ++r) acc[r] += Pol::wmul(w, v[r][q]);
               }
             while (rm) {
               const int k = __ffs(rm) - 1;
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
               for (int r = 0; r < R; ++r) {
                 const S* sp = src_row[r][t.bond_ia[k]];
-                if (((dr[r] >> k) & 1u) && sp) acc[r] += Pol::bw(t, k) * __ldg(sp + mq);
+                if (((dr[r] >> k) & 1u) && sp) acc[r] += Pol::wmul(Pol::bw(t, k), __ldg(sp + mq));
               }
             }
           }
@@ -382,7 +382,7 @@ static __device__ __align__(16) long long g_zero_row[256];
 // their loads carry no predicates.
 template <class Pol, int NC, int U>
 __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ items, long long n_items,
-                                                const typename Pol::S* __restrict__ x, typename Pol::S* __restrict__ y,
+                                                const typename Pol::S* __restrict__ x, typename Pol::Y* __restrict__ y,
                                                 const int* __restrict__ emax) {
   using S = typename Pol::S;
   constexpr int W = 32 * NC;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
     const long long gA = bl.gA0 + a;
     const long long dB = bl.dB;
     const S* xb = x + bl.off;
-    S* yrow = y + bl.off + a * dB;
+    typename Pol::Y* yrow = y + bl.off + a * dB;
     const uint2 m = t.A_meta[gA];
     for (int sp = 0; sp < 256; sp += W) {
       const long long b0 = it.y + sp + lane;
@@ -406,11 +406,11 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
       const bool full = it.y + sp + W <= dB;
       const S* xb0 = xb + b0;                                              // column b0 of row 0
       const S* zr = reinterpret_cast<const S*>(g_zero_row) + lane;         // zeros at +32c
-      S acc[NC];
+      typename Pol::Y acc[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const long long b = b0 + 32 * c;
-        acc[c] = b < dB ? yrow[b] : (S)0;
+        acc[c] = b < dB ? yrow[b] : (typename Pol::Y)0;
       }
       unsigned e = m.x;
 #pragma unroll
@@ -458,9 +458,9 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
         }
         }
         e += n;
-        const S wc = Pol::w(t, cl);
+        const typename Pol::W wc = Pol::w(t, cl);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += wc * sum[c];
+        for (int c = 0; c < NC; ++c) acc[c] += Pol::wmul(wc, sum[c]);
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -529,7 +529,7 @@ struct ProfMarks {
 };
 
 template <class Pol>
-static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::S* y, const int* emax, cudaStream_t st,
+static ed_status run_v3(ed_ctx* c, const typename Pol::S* x, typename Pol::Y* y, const int* emax, cudaStream_t st,
                         ProfMarks& pm) {
   P3 p = make_p3(c);
   if (p.n_rows == 0) return ED_OK;
@@ -609,11 +609,18 @@ static ed_status apply_fixed(ed_ctx* c, const double* x, double* y, long long* f
   pm.mark(1, st);
   k_to_fixed<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>(x, fixed, n, emax, c->t3.P);
   ED_CUDA_TRY(cudaGetLastError());
-  ED_TRY(run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm));
-  return diag_add(c, x, y, st);
+  if (c->dyadic) {
+    ED_TRY(run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm));
+    return diag_add(c, x, y, st);
+  }
+  return run_v3<PC64>(c, fixed, y, emax, st, pm);
 }
 
-bool fixed_path(const ed_ctx* c, const void* x) { return c->dyadic && v3_usable(c, ED_F64, x); }
+// fixed-point input: exact integer sums, either with integer weights (dyadic
+// couplings) or with FP64 weights per value class
+static bool fixed_mode(const ed_ctx* c) { return c->dyadic || c->classed; }
+
+bool fixed_path(const ed_ctx* c, const void* x) { return fixed_mode(c) && v3_usable(c, ED_F64, x); }
 
 ed_status apply_prepared_fixed(ed_ctx* c, const double* x, double* y, cudaStream_t st) {
   if (!c->d_fixed) {
@@ -624,8 +631,13 @@ ed_status apply_prepared_fixed(ed_ctx* c, const double* x, double* y, cudaStream
   pm.begin(c);
   pm.mark(0, st);
   pm.mark(1, st);
-  ed_status r = run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st, pm);
-  if (r == ED_OK) r = diag_add(c, x, y, st);
+  ed_status r;
+  if (c->dyadic) {
+    r = run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st, pm);
+    if (r == ED_OK) r = diag_add(c, x, y, st);
+  } else {
+    r = run_v3<PC64>(c, c->d_fixed, y, c->d_exp, st, pm);
+  }
   pm.mark(4, st);
   pm.end(c);
   return r;
@@ -635,7 +647,7 @@ ed_status apply_v3(ed_ctx* c, const void* x, void* y, ed_dtype dt, cudaStream_t 
   ProfMarks pm;
   pm.begin(c);
   ed_status r;
-  if (dt == ED_F32 || !c->dyadic) {
+  if (dt == ED_F32 || !fixed_mode(c)) {
     pm.mark(0, st);
     pm.mark(1, st);
     r = dt == ED_F32 ? run_v3<PF32>(c, (const float*)x, (float*)y, nullptr, st, pm)
@@ -694,7 +706,7 @@ extern "C" ed_status ed_apply_H_noalloc(ed_ctx* c, const void* x, void* y, void*
   if (!c->ops_built) { set_error("ed_build_local_ops has not been called"); return ED_EINVAL; }
   if (c->D > 0 && (!x || !y)) { set_error("x or y is NULL"); return ED_EINVAL; }
   const size_t need = kNoAllocHeader + (size_t)c->D * sizeof(long long);
-  if (c->dyadic && need > kNoAllocScratchBytes) {
+  if (fixed_mode(c) && need > kNoAllocScratchBytes) {
     set_error("ed_apply_H_noalloc: %lld states need %zu bytes of scratch, the static scratch holds %zu "
               "(at most %zu states)", (long long)c->D, need, kNoAllocScratchBytes,
               (kNoAllocScratchBytes - kNoAllocHeader) / sizeof(long long));
@@ -711,7 +723,7 @@ extern "C" ed_status ed_apply_H_noalloc(ed_ctx* c, const void* x, void* y, void*
   ED_DEVICE_SCOPE(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   ProfMarks pm;  // no profiling events here
-  if (!c->dyadic) return run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st, pm);
+  if (!fixed_mode(c)) return run_v3<PF64>(c, (const double*)x, (double*)y, nullptr, st, pm);
   unsigned char* base = nullptr;
   ED_TRY(noalloc_scratch(c->device, &base));
   return apply_fixed(c, (const double*)x, (double*)y, (long long*)(base + kNoAllocHeader), (int*)base, st, pm);

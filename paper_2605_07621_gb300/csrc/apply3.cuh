@@ -1,6 +1,7 @@
 // Device code shared by the class-sorted H|psi> kernels (paper Eq. (2)):
-// the kernel parameter block, the three arithmetic policies (FP32, FP64,
-// exact 64-bit fixed point), the fixed-point <-> FP64 conversions done by
+// the kernel parameter block, the arithmetic policies (FP32, FP64, exact
+// 64-bit fixed point, fixed-point sums with FP64 weights), the fixed-point
+// <-> FP64 conversions done by
 // bit manipulation, and the TMA / mbarrier helpers.
 #pragma once
 
@@ -21,8 +22,16 @@ struct P3 {
   int keep_fixed;  // row pass leaves every row as a 64-bit partial sum (cross terms added later)
 };
 
+// Policy types: S = staged / gathered values (and per-class sums), Y = the
+// accumulator and the partial output kept in y between the passes, D = the
+// diagonal, W = the per-class weights; dmul / wmul combine them.
 struct PF32 {
   using S = float;
+  using Y = float;
+  using D = float;
+  using W = float;
+  __device__ static float dmul(float d, float x) { return d * x; }
+  __device__ static float wmul(float w, float s) { return w * s; }
   __device__ static float w(const Dev3& t, int c) { return t.w32[c]; }
   __device__ static float bw(const Dev3& t, int k) { return t.bond_w32[k]; }
   __device__ static float diagA(const Dev3& t, long long gA) { return t.A_d32[gA] + t.dc0_32; }
@@ -40,6 +49,11 @@ struct PF32 {
 };
 struct PF64 {
   using S = double;
+  using Y = double;
+  using D = double;
+  using W = double;
+  __device__ static double dmul(double d, double x) { return d * x; }
+  __device__ static double wmul(double w, double s) { return w * s; }
   __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
   __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
   __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
@@ -57,6 +71,11 @@ struct PF64 {
 };
 struct PI64 {
   using S = long long;
+  using Y = long long;
+  using D = long long;
+  using W = long long;
+  __device__ static long long dmul(long long d, long long x) { return d * x; }
+  __device__ static long long wmul(long long w, long long s) { return w * s; }
   __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
   __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
   __device__ static long long diagA(const Dev3& t, long long gA) { return (long long)t.A_dI[gA] + t.dc0_I; }
@@ -71,6 +90,26 @@ struct PI64 {
     for (int q = 0; q < t.ncls_d; ++q) v += t.dwI[q] * (long long)__popc(z & t.dmask[q]);
     return v;
   }
+};
+
+// Fixed-point gathers with FP64 weights (models whose couplings are not
+// dyadic): x is summed exactly per value class on the integer pipe as in
+// PI64, and each class sum is multiplied by its FP64 weight once per
+// element, the diagonal likewise (a few FP64 operations per element instead
+// of one per matrix element).  The partial result between the passes is FP64
+// in fixed-point units; the last store scales it by one power of two.
+struct PC64 {
+  using S = long long;
+  using Y = double;
+  using D = double;
+  using W = double;
+  __device__ static double dmul(double d, long long x) { return d * (double)x; }
+  __device__ static double wmul(double w, long long s) { return w * (double)s; }
+  __device__ static double w(const Dev3& t, int c) { return t.w64[c]; }
+  __device__ static double bw(const Dev3& t, int k) { return t.bond_w64[k]; }
+  __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
+  __device__ static double diagB(const Dev3& t, long long gB) { return t.B_d64[gB]; }
+  __device__ static double vab(const Dev3& t, unsigned z) { return PF64::vab(t, z); }
 };
 
 // ---------------------------------------------------------------- fixed point <-> FP64 by bit manipulation
@@ -152,7 +191,7 @@ __host__ __device__ __forceinline__ double from_fixed(long long Y, int e2) {
 __device__ __forceinline__ int out_exp(const Dev3& t, const int* emax) { return (emax[0] - 1022) - t.P - t.q_shift; }
 
 template <class Pol>
-__device__ __forceinline__ void store_out(typename Pol::S* y, long long i, typename Pol::S v, bool final_,
+__device__ __forceinline__ void store_out(typename Pol::Y* y, long long i, typename Pol::Y v, bool final_,
                                           int e2) {
   y[i] = v;
 }
@@ -160,6 +199,10 @@ template <>
 __device__ __forceinline__ void store_out<PI64>(long long* y, long long i, long long v, bool final_, int e2) {
   if (final_) reinterpret_cast<double*>(y)[i] = from_fixed(v, e2);
   else y[i] = v;
+}
+template <>
+__device__ __forceinline__ void store_out<PC64>(double* y, long long i, double v, bool final_, int e2) {
+  y[i] = final_ ? ldexp(v, e2) : v;
 }
 
 // ---------------------------------------------------------------- TMA / mbarrier

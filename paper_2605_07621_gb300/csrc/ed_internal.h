@@ -265,6 +265,8 @@ struct ed_ctx {
   // class-sorted path
   bool v3_ok = false;                // tables below are valid
   bool dyadic = false;               // FP64 apply may use exact fixed point
+  bool classed = false;              // couplings not dyadic: the FP64 apply sums the fixed-point
+                                     // input exactly per value class and weights each sum in FP64
   bool diag_split = false;           // ... for the off-diagonal terms only; the
                                      // diagonal is added in FP64 afterwards
   edk::Dev3 t3{};

@@ -291,6 +291,21 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
     c->dyadic = t.P >= 40;
   }
   if (!c->dyadic) c->diag_split = false;
+  // couplings that are not dyadic: fixed-point input summed exactly per value
+  // class (at most the largest per-class count of one row's terms in one
+  // pass, plus the cross bonds), each class sum weighted in FP64
+  c->classed = false;
+  if (!c->dyadic) {
+    long long mx = 1;
+    for (const Side3* s3 : {&a3, &b3})
+      for (const uint2& m : s3->meta)
+        for (int cc = 0; cc < kMaxCls; ++cc) mx = std::max<long long>(mx, (m.y >> (8 * cc)) & 255u);
+    mx += (long long)c->cross.size();
+    const int bits = (int)std::ceil(std::log2((double)mx + 1.0));
+    t.q_shift = 0;
+    t.P = std::min(60, 62 - bits);
+    c->classed = t.P >= 40;
+  }
   // upload
   uint2 *Am, *Bm;
   uint16_t *Ac, *Bc, *mA, *mB;

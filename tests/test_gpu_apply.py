@@ -173,6 +173,17 @@ def test_j1j2_4x8_sampled_rows(ed, oracle_mod):
     assert err[torch.float32] <= TOL32
 
 
+def test_j1j2_4x8_nondyadic_sampled_rows(ed, oracle_mod):
+    """J2 = 0.3 (J2/2 = 0.15 is not a dyadic rational): the FP64 apply sums the
+    fixed-point input exactly per value class and weights each class sum in
+    FP64; sampled rows of the full 601,080,390-state vector against the oracle."""
+    import torch
+
+    err = _sampled_rows(ed, oracle_mod, W.j1j2_torus(8, 4, 1.0, 0.3, 16, 0xFFFF), 300, 2000)
+    assert err[torch.float64] <= TOL64
+    assert err[torch.float32] <= TOL32
+
+
 def _dyadic_spin(m):
     """Every spin matrix element (J_xy/2, J_z/4) is a multiple of 2^-20, so
     the FP64 apply runs in exact fixed point."""
