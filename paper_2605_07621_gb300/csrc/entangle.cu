@@ -7,66 +7,21 @@
 // its nonzero eigenvalues are those of the Gram matrix of Psi_s in the
 // smaller of its two dimensions (the squared singular values of Psi_s).
 // The Gram matrix is formed on the tensor cores by the FP64-accurate
-// digit-split GEMM (ozaki.cu; one digit-plane buffer serves as both factors,
-// only the tiles on or below the diagonal are computed: the matrix is
-// symmetric); the eigenvalues of each Gram matrix come from cuSOLVER's dense
-// symmetric divide-and-conquer eigensolver, which is loaded with dlopen on
-// the first call so that the rest of the library does not depend on it.
-#include <dlfcn.h>
-
+// digit-split GEMM (ozaki.cu; one digit-plane buffer serves as both
+// factors, only the tiles on or below the diagonal), reduced to tridiagonal form on the GPU by Householder
+// reflections, and its eigenvalues come from implicit-shift QL on the host,
+// one thread per block while the GPU reduces the next block (eigsym.cu).
 #include <cmath>
-#include <mutex>
-
-#include <cusolverDn.h>
+#include <algorithm>
+#include <chrono>
+#include <thread>
 
 #include "krylov.h"
+#include "eigsym.h"
 #include "ozaki.h"
 
 namespace edk {
 namespace {
-
-// the five cuSOLVER entry points used here, resolved once
-struct Solver {
-  using create_t = cusolverStatus_t (*)(cusolverDnHandle_t*);
-  using destroy_t = cusolverStatus_t (*)(cusolverDnHandle_t);
-  using stream_t = cusolverStatus_t (*)(cusolverDnHandle_t, cudaStream_t);
-  using bufsize_t = cusolverStatus_t (*)(cusolverDnHandle_t, cusolverEigMode_t, cublasFillMode_t, int, const double*,
-                                         int, const double*, int*);
-  using syevd_t = cusolverStatus_t (*)(cusolverDnHandle_t, cusolverEigMode_t, cublasFillMode_t, int, double*, int,
-                                       double*, double*, int, int*);
-  create_t create = nullptr;
-  destroy_t destroy = nullptr;
-  stream_t set_stream = nullptr;
-  bufsize_t bufsize = nullptr;
-  syevd_t syevd = nullptr;
-  bool ok = false;
-  std::string why;
-};
-
-const Solver& solver() {
-  static Solver s;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* h = nullptr;
-    for (const char* name : {"libcusolver.so.12", "libcusolver.so.11", "libcusolver.so"}) {
-      h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
-      if (h) break;
-    }
-    if (!h) {
-      const char* e = dlerror();
-      s.why = std::string("cannot load cuSOLVER: ") + (e ? e : "unknown");
-      return;
-    }
-    s.create = (Solver::create_t)dlsym(h, "cusolverDnCreate");
-    s.destroy = (Solver::destroy_t)dlsym(h, "cusolverDnDestroy");
-    s.set_stream = (Solver::stream_t)dlsym(h, "cusolverDnSetStream");
-    s.bufsize = (Solver::bufsize_t)dlsym(h, "cusolverDnDsyevd_bufferSize");
-    s.syevd = (Solver::syevd_t)dlsym(h, "cusolverDnDsyevd");
-    s.ok = s.create && s.destroy && s.set_stream && s.bufsize && s.syevd;
-    if (!s.ok) s.why = "cuSOLVER lacks the dense symmetric eigensolver entry points";
-  });
-  return s;
-}
 
 struct DevMem {
   std::vector<void*> p;
@@ -82,13 +37,6 @@ struct DevMem {
     }
     p.push_back(*out);
     return ED_OK;
-  }
-};
-
-struct Handle {
-  cusolverDnHandle_t h = nullptr;
-  ~Handle() {
-    if (h) solver().destroy(h);
   }
 };
 
@@ -128,36 +76,17 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     set_error("lambda holds %lld values, %lld needed", (long long)cap, (long long)need);
     return ED_EINVAL;
   }
-  if (mmax > 46340) {  // m * m must fit the eigensolver's int sizes
+  if (mmax > 46340) {  // m * m must fit 32-bit index arithmetic of the reduction
     set_error("block Gram dimension %lld exceeds the dense eigensolver's limit", (long long)mmax);
-    return ED_EUNSUPPORTED;
-  }
-  const Solver& S = solver();
-  if (!S.ok) {
-    set_error("%s", S.why.c_str());
     return ED_EUNSUPPORTED;
   }
   ED_DEVICE_SCOPE(c->device);
   ED_TRY(ensure_scratch(c));
   cudaStream_t st = (cudaStream_t)stream;
-  Handle H;
-  if (S.create(&H.h) != CUSOLVER_STATUS_SUCCESS || S.set_stream(H.h, st) != CUSOLVER_STATUS_SUCCESS) {
-    set_error("cuSOLVER handle creation failed");
-    return ED_ECUDA;
-  }
   DevMem mem;
-  double *G = nullptr, *W = nullptr, *work = nullptr;
-  int* info = nullptr;
+  double *G = nullptr, *work = nullptr;
   ED_TRY(mem.get((void**)&G, (size_t)mmax * mmax * sizeof(double)));
-  ED_TRY(mem.get((void**)&W, (size_t)mmax * sizeof(double)));
-  ED_TRY(mem.get((void**)&info, sizeof(int)));
-  int lwork = 0;
-  if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_UPPER, (int)mmax, G, (int)mmax, W, &lwork) !=
-      CUSOLVER_STATUS_SUCCESS) {
-    set_error("cuSOLVER workspace query failed");
-    return ED_ECUDA;
-  }
-  ED_TRY(mem.get((void**)&work, (size_t)std::max(lwork, 1) * sizeof(double)));
+  ED_TRY(mem.get((void**)&work, (size_t)tridiag_work_doubles((int)mmax) * sizeof(double)));
 
   // digit planes of one block at a time (both factors of its Gram matrix),
   // tensor maps and launch lists of every block built up front
@@ -203,7 +132,7 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     p.K = L;
     p.acc = 0;
     p.tiles_n = (m + kOzBN - 1) / kOzBN;
-    p.tri = 1;
+    p.tri = 1;  // the lower triangle: all the reduction reads
     p.tile0 = 0;
     probs.push_back(p);
     tiles.push_back(oz_tiles(m, m, 1));
@@ -216,13 +145,34 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
   ED_CUDA_TRY(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(OzSliceJob), cudaMemcpyHostToDevice));
   ED_CUDA_TRY(cudaMemcpy(d_probs, probs.data(), probs.size() * sizeof(OzProblem), cudaMemcpyHostToDevice));
 
-  std::vector<double> w(mmax);
   std::vector<double> wt(c->blocks.size());
+  // per block: its tridiagonal matrix, handed to a host thread for the QL
+  // steps while the GPU forms and reduces the next block
+  std::vector<std::vector<double>> dd(c->blocks.size()), ee(c->blocks.size());
+  std::vector<char> ok(c->blocks.size(), 1);
+  std::vector<std::thread> qr;
+  struct Joiner {
+    std::vector<std::thread>* t;
+    ~Joiner() {
+      for (auto& x : *t)
+        if (x.joinable()) x.join();
+    }
+  } joiner{&qr};
   Events ev;
   for (cudaEvent_t& x : ev.e) ED_CUDA_TRY(cudaEventCreate(&x));
-  double t_gram = 0.0, t_eig = 0.0;
-  int64_t pos = 0;
-  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+  double t_gram = 0.0, t_red = 0.0;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  // largest blocks first: their host QL runs while the GPU handles the rest
+  std::vector<size_t> order(c->blocks.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t u, size_t v) {
+    return std::min(c->blocks[u].dA, c->blocks[u].dB) > std::min(c->blocks[v].dA, c->blocks[v].dB);
+  });
+  for (size_t bi : order) {
     const Block& b = c->blocks[bi];
     const double* xb = psi + b.off;
     const int m = (int)std::min(b.dA, b.dB);
@@ -231,22 +181,10 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     ED_TRY(oz_slice(&oz, d_jobs + bi, 1, units[bi], b.dA > b.dB, nullptr, st));
     ED_TRY(oz_gemm(&oz, d_probs + bi, 1, tiles[bi], nullptr, st));
     ED_CUDA_TRY(cudaEventRecord(ev.e[1], st));
-    int lw = 0;
-    if (S.bufsize(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_UPPER, m, G, m, W, &lw) !=
-            CUSOLVER_STATUS_SUCCESS ||
-        lw > lwork) {
-      set_error("cuSOLVER workspace for dimension %d exceeds the one allocated", m);
-      return ED_ECUDA;
-    }
-    if (S.syevd(H.h, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_UPPER, m, G, m, W, work, lwork, info) !=
-        CUSOLVER_STATUS_SUCCESS) {
-      set_error("cuSOLVER eigensolver failed on block %zu (dimension %d)", bi, m);
-      return ED_ECUDA;
-    }
+    dd[bi].assign(m, 0.0);
+    ee[bi].assign(std::max(m - 1, 1), 0.0);
+    ED_TRY(tridiag_reduce(G, m, work, dd[bi].data(), ee[bi].data(), st, sms));
     ED_CUDA_TRY(cudaEventRecord(ev.e[2], st));
-    int hinfo = 0;
-    ED_CUDA_TRY(cudaMemcpyAsync(w.data(), W, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
-    ED_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
     // ||Psi_s||^2 (the trace of rho_A(s)) with the library's FP64 reduction
     ED_TRY(dot_dev<double>(c, xb, xb, b.dA * b.dB, slot(c, 3), st, 0));
     ED_TRY(read_scalars(c, 3, 1, &wt[bi], st));  // synchronises the stream
@@ -254,17 +192,27 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     ED_CUDA_TRY(cudaEventElapsedTime(&t1, ev.e[0], ev.e[1]));
     ED_CUDA_TRY(cudaEventElapsedTime(&t2, ev.e[1], ev.e[2]));
     t_gram += t1;
-    t_eig += t2;
-    if (hinfo != 0) {
-      set_error("cuSOLVER eigensolver reported info=%d on block %zu", hinfo, bi);
-      return ED_ECUDA;
+    t_red += t2;
+    ee[bi].resize(std::max(m - 1, 0));
+    qr.emplace_back([&dd, &ee, &ok, bi] { ok[bi] = tridiag_eigenvalues(dd[bi], ee[bi]) ? 1 : 0; });
+  }
+  const auto tq = std::chrono::steady_clock::now();
+  for (auto& x : qr) x.join();
+  const double t_qr = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tq).count();
+  int64_t pos = 0;
+  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+    if (!ok[bi]) {
+      set_error("tridiagonal QL did not converge on block %zu", bi);
+      return ED_ENOCONV;
     }
-    for (int i = 0; i < m; ++i) lambda[pos + i] = w[m - 1 - i];  // descending
-    pos += m;
+    std::vector<double>& w = dd[bi];
+    std::sort(w.begin(), w.end(), [](double u, double v) { return u > v; });  // descending
+    for (size_t i = 0; i < w.size(); ++i) lambda[pos + i] = w[i];
+    pos += (int64_t)w.size();
   }
   if (stage_ms) {
     stage_ms[0] = t_gram;
-    stage_ms[1] = t_eig;
+    stage_ms[1] = t_red + t_qr;  // GPU reduction plus the host QL left after the last block
   }
   double tot = 0.0;
   for (double v : wt) tot += v;
