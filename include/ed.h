@@ -203,9 +203,11 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  * charge s of side A, with the sector weights W_s = sum_i lambda_{s,i} /
  * sum_{s,i} lambda_{s,i}.  rho_A is block diagonal, rho_A(s) = Psi_s Psi_s^T;
  * its nonzero eigenvalues are those of the Gram matrix of Psi_s in the
- * smaller of d_A(s), d_B(s), formed in FP64 on the device by this library;
- * the eigenvalues of each Gram matrix come from cuSOLVER's dense symmetric
- * eigensolver (loaded on the first call; ED_EUNSUPPORTED without it).
+ * smaller of d_A(s), d_B(s), formed on the device by this library; its
+ * eigenvalues come from a Householder reduction to tridiagonal form on the
+ * device and implicit QL steps on the host (one host thread per block, in
+ * parallel with the device work of the next block; ED_ENOCONV if a QL
+ * iteration does not converge).
  *   psi      device FP64 vector of ctx (not normalised by the call)
  *   lambda   host, capacity cap: for every block in ed_blocks order, its
  *            min(d_A, d_B) eigenvalues in descending order (rounding can
@@ -215,14 +217,17 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  *   weight   host, one per block (nullable): ||Psi_s||^2 = trace rho_A(s),
  *            summed on the device in FP64
  *   entropy  host (nullable): -sum p ln p over p = lambda / sum(weight) > 0
- *   stage_ms host (nullable), 2 doubles: device time of the Gram kernels and
- *            of the eigensolver, summed over the blocks (CUDA events)
+ *   stage_ms host (nullable), 2 doubles: device time of the Gram kernels, and
+ *            the device time of the tridiagonal reductions plus the host QL
+ *            time left after the last block (milliseconds)
  * The Gram matrices are formed on the tensor cores in FP64-accurate
  * digit-split form (8 BF16 digit planes per value, exact FP32 sums per digit
  * order, FP64 combination).  Device memory: one Gram matrix of the largest
- * block (8 min(dA,dB)^2 bytes), the digit planes of one block (16 bytes per
- * element) and the eigensolver workspace; blocks with min(dA,dB) > 46340 are
- * ED_EUNSUPPORTED.  Synchronises the stream. */
+ * block (8 min(dA,dB)^2 bytes; only its lower triangle is formed and
+ * reduced), the digit planes of one block (16 bytes per element) and the
+ * reduction's workspace (about m^2 / 2 bytes for the largest m = min(dA,dB));
+ * blocks with min(dA,dB) > 46340 are ED_EUNSUPPORTED.  Synchronises the
+ * stream. */
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
                                    double* weight, double* entropy, double* stage_ms, void* stream);
 
