@@ -348,7 +348,7 @@ def batched_and_served(ed, n: int, rate: float, seed: int = 20260507, rank: int 
     t0 = time.perf_counter()
     b = ed.batch_create(models)
     t_create = time.perf_counter() - t0
-    thr, tune = b.info()
+    modes, tune = b.info()
     # one batched H|psi> over all instances (FP32), device-timed
     x = torch.ones(b.dim, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
@@ -362,12 +362,31 @@ def batched_and_served(ed, n: int, rate: float, seed: int = 20260507, rank: int 
     e1.record()
     torch.cuda.synchronize()
     apply_ms = e0.elapsed_time(e1) / 5
+    # roofline of the batched apply: HBM bytes of read x + write y (FP32),
+    # and the tensor-core FLOPs of the dense instances (six BF16 piece
+    # products per multiply-add of H_A Psi + Psi H_B^T) over the whole apply
+    from math import comb
+    dims = [(comb(m.n_sites, m.n_up), comb(m.n_sites, m.n_dw)) for m in models]
+    D = sum(a * bb for a, bb in dims)
+    dense_flops = sum(6 * 2 * a * bb * (a + bb) for (a, bb), md in zip(dims, modes) if md > 0)
+    peaks, peak_src = measured_peaks()
+    gbs = 8 * D / (apply_ms * 1e-3) / 1e9
+    tfl = dense_flops / (apply_ms * 1e-3) / 1e12
+    apply_roof = {"hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                          "bytes": 8 * D, "peak_source": peak_src},
+                  "tensor": {"achieved": tfl, "peak": bf16_peak()[0], "unit": "TFLOP/s",
+                             "frac": tfl / bf16_peak()[0], "flops": dense_flops, "peak_source": bf16_peak()[1],
+                             "note": "BF16 piece products of the dense instances over the whole apply time"}}
     t0 = time.perf_counter()
     e, it, info = ed.batch_lanczos(b, tol=1e-7)
     t_solve = time.perf_counter() - t0
     batched = {"workload": f"{n} Hubbard instances (8-12 sites, random fillings, U, t', eps)", "states": int(b.dim),
-               "create_s": t_create, "dense_threshold": int(thr), "tune_ms": [float(v) for v in tune],
-               "apply_ms": apply_ms, "solve_s": t_solve, "instances_per_s": n / t_solve,
+               "create_s": t_create,
+               "modes": {"csr": int(np.sum(modes == 0)), "dense_64": int(np.sum(modes == 1)),
+                         "dense_128": int(np.sum(modes == 2))},
+               "tune_ms": {"all_csr": float(tune[0]), "all_dense_64": float(tune[1]),
+                           "all_dense_128": float(tune[2]), "tuned": float(tune[3])},
+               "apply_ms": apply_ms, "apply_roofline": apply_roof, "solve_s": t_solve, "instances_per_s": n / t_solve,
                "hpsi_per_s_aggregate": float(np.sum(it)) / t_solve, "steps": info["steps"],
                "all_converged": info["all_converged"], "storage": "f32", "reductions": "f64"}
     del x, y, b

@@ -263,20 +263,38 @@ void ed_dense_destroy(ed_dense* d);
 /* ---- batched form -------------------------------------------------------
  * Many independent single-block instances (Hubbard models with the spin
  * cut) packed into one device arena and stepped together: every kernel is
- * one persistent launch over all (instance, row) or (instance, chunk) work
- * items of the active instances, and the whole Lanczos step (apply, FP64
- * reductions, vector update) is one captured CUDA graph replayed each step.
- * Per instance, H_A is applied from its CSR or, for small d_A, from a dense
- * d_A x d_A table; the d_A threshold is chosen by timing the batched apply
- * (ED_OPS_DEFAULT) or pinned by ED_OPS_FORCE_CSR / ED_OPS_FORCE_DENSE.
- * Vectors are FP32; reductions are FP64-accurate. */
+ * one persistent launch over all (instance, row), (instance, tile) or
+ * (instance, chunk) work items of the active instances, and the whole
+ * Lanczos step (apply, FP64 reductions, vector update) is one captured CUDA
+ * graph replayed each step.  Eq. (2) for one block with the spin cut (no
+ * cross terms): H psi = H_A Psi + Psi H_B^T + V o Psi.  Per instance, H psi
+ * runs in one of three modes:
+ *   0  CSR: the side operators as sparse rows, one warp per row of Psi;
+ *   1  dense on the tensor cores, 128 x 64 output tiles;
+ *   2  dense on the tensor cores, 128 x 128 output tiles.
+ * The dense modes (instances with d_A, d_B <= 1024) hold H_A and H_B as
+ * dense matrices and form both products with BF16 tcgen05 MMAs and FP32
+ * accumulation, every FP32 operand split into three BF16 pieces (24
+ * significant bits; piece products of order <= 2 kept), so the result has
+ * FP32 accuracy.  flags: ED_OPS_DEFAULT times every mode on each instance
+ * shape (d_A, d_B, nonzeros of H_A and H_B) and keeps the fastest, cached
+ * per process (so a shape is timed once); ED_OPS_FORCE_CSR uses mode 0 and
+ * allocates no dense tables; ED_OPS_FORCE_DENSE uses mode 1 when d_B <= 64,
+ * else 2, wherever the instance has a dense form.
+ * Vectors are FP32; reductions are FP64-accurate.  A tensor-core wait that
+ * runs out (it should not) sets an error flag; the next ed_batch_lanczos
+ * or ed_batch_create then returns ED_ETIMEOUT. */
 typedef struct ed_batch ed_batch;
 ed_status ed_batch_create(const ed_model_desc* models, int n, int flags, ed_batch** out);
 /* total elements of the concatenated layout (instance i at off[i]) */
 int64_t ed_batch_dim(const ed_batch* b);
 ed_status ed_batch_offsets(const ed_batch* b, int64_t* off /* n+1, host */);
-/* chosen dense threshold and the timed apply (ms) for thresholds 0,8,16,32,64 */
-ed_status ed_batch_info(const ed_batch* b, int* dense_threshold, float* tune_ms /* 5, nullable */);
+/* modes: host n ints (nullable), the mode of each instance (0, 1, 2 above);
+ * tune_ms: host 4 floats (nullable), device time of one batched H psi with
+ * every instance in mode 0, in mode 1, in mode 2 (where it has a dense
+ * form), and with the chosen modes; under a forced flag only the last is
+ * measured, the others are 0 */
+ed_status ed_batch_info(const ed_batch* b, int* modes, float* tune_ms);
 /* y = H x for all instances (device FP32 vectors in the concatenated layout) */
 ed_status ed_batch_apply(ed_batch* b, const void* x, void* y, ed_dtype dtype, void* stream);
 /* ground-state energies of all instances (mode ED_LZ_F32; tol: relative

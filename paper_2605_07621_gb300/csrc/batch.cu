@@ -7,8 +7,14 @@
 #include <cstring>
 #include <memory>
 
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "batch.h"
+#include "batch_dev.cuh"
 #include "krylov.h"
+#include "ozaki.h"
 #include "reduce.cuh"
 #include "splitmix.cuh"
 
@@ -17,34 +23,41 @@ namespace edk {
 constexpr int kBW = 8;          // warps per CTA in the apply kernel
 constexpr int kBStage = 1024;   // row elements staged in shared memory per warp
 
-__device__ __forceinline__ int find_pref(const long long* pref, int n, long long v) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (pref[mid] <= v) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// y = H x for every active instance; one warp per row a (lanes over b).
-// user_mode: x, y are a caller's concatenated vectors (offset uoff);
-// otherwise v -> w inside each instance's arena triple.
+// y = H x for the active instances in CSR mode; one warp per row a (lanes
+// over b).  user_mode: x, y are a caller's concatenated vectors (offset
+// uoff); otherwise v -> w inside each instance's arena triple.
 __global__ void __launch_bounds__(256) k_bapply(const BInst* __restrict__ insts, const int* __restrict__ idx,
-                                                const long long* __restrict__ rowpref, const int* __restrict__ nact,
+                                                const long long* __restrict__ rowpref, const int* __restrict__ cnt,
                                                 const float* __restrict__ ux, float* __restrict__ uy, float* arena,
                                                 int user_mode) {
   __shared__ float stage[kBW][kBStage];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = *nact;
+  const int n = cnt[0];
   if (n <= 0) return;
   const long long total = rowpref[n];
   for (long long row = (long long)blockIdx.x * kBW + warp; row < total; row += (long long)gridDim.x * kBW) {
     const int ai = find_pref(rowpref, n, row);
     const BInst& I = insts[idx[ai]];
     const long long a = row - rowpref[ai];
-    const int dA = I.dA, dB = I.dB;
-    const float* x = user_mode ? ux + I.uoff : arena + I.voff + I.D;
-    float* y = user_mode ? uy + I.uoff : arena + I.voff + 2 * I.D;
+    // the instance's fields in registers (y stores could alias them otherwise)
+    const int dB = I.dB;
+    const float* __restrict__ x = user_mode ? ux + I.uoff : arena + I.voff + I.D;
+    float* __restrict__ y = user_mode ? uy + I.uoff : arena + I.voff + 2 * I.D;
+    const int* __restrict__ Brp = I.B_rp;
+    const int* __restrict__ Bcol = I.B_col;
+    const float* __restrict__ Bval = I.B_val;
+    const float* __restrict__ Bd = I.B_diag;
+    const uint32_t* __restrict__ Bs = I.B_str;
+    const int* __restrict__ Acol = I.A_col;
+    const float* __restrict__ Aval = I.A_val;
+    const int ncls = I.ncls, vand = I.vab_and;
+    float w[kMaxClasses];
+    unsigned mk[kMaxClasses];
+#pragma unroll
+    for (int q = 0; q < kMaxClasses; ++q) {
+      w[q] = I.w[q];
+      mk[q] = I.mask[q];
+    }
     const float* xrow = x + a * dB;
     const bool staged = dB <= kBStage;
     if (staged) {
@@ -55,20 +68,15 @@ __global__ void __launch_bounds__(256) k_bapply(const BInst* __restrict__ insts,
     const float da = I.A_diag[a] + I.c0;
     const uint32_t sa = I.A_str[a];
     const int ea0 = I.A_rp[a], ea1 = I.A_rp[a + 1];
-    const float* Drow = I.use_dense ? I.A_dense + a * dA : nullptr;
     for (int b = lane; b < dB; b += 32) {
-      const uint32_t sb = I.B_str[b];
-      const uint32_t z = I.vab_and ? (sa & sb) : (sa ^ sb);
-      float v = da + I.B_diag[b];
-      for (int q = 0; q < I.ncls; ++q) v += I.w[q] * (float)__popc(z & I.mask[q]);
+      const uint32_t sb = Bs[b];
+      const uint32_t z = vand ? (sa & sb) : (sa ^ sb);
+      float v = da + Bd[b];
+      for (int q = 0; q < ncls; ++q) v += w[q] * (float)__popc(z & mk[q]);
       float acc = v * xs[b];
-      const int eb0 = I.B_rp[b], eb1 = I.B_rp[b + 1];
-      for (int e = eb0; e < eb1; ++e) acc += I.B_val[e] * xs[I.B_col[e]];
-      if (Drow) {
-        for (int a2 = 0; a2 < dA; ++a2) acc += Drow[a2] * x[(long long)a2 * dB + b];
-      } else {
-        for (int e = ea0; e < ea1; ++e) acc += I.A_val[e] * x[(long long)I.A_col[e] * dB + b];
-      }
+      const int eb0 = Brp[b], eb1 = Brp[b + 1];
+      for (int e = eb0; e < eb1; ++e) acc += Bval[e] * xs[Bcol[e]];
+      for (int e = ea0; e < ea1; ++e) acc += Aval[e] * x[(long long)Acol[e] * dB + b];
       y[a * dB + b] = acc;
     }
     __syncwarp();
@@ -231,7 +239,7 @@ struct HostTables {
   int64_t dA = 0, dB = 0;
   int n_sites = 0;
   std::vector<int> A_rp, A_col, B_rp, B_col;
-  std::vector<float> A_val, B_val, A_diag, B_diag, A_dense;
+  std::vector<float> A_val, B_val, A_diag, B_diag;
   std::vector<uint32_t> A_str, B_str;
   float c0 = 0.f;
   int ncls = 0, vab_and = 0;
@@ -240,6 +248,7 @@ struct HostTables {
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+int pad8(int64_t d) { return (int)((d + 7) / 8 * 8); }
 
 ed_status host_tables(const ed_model_desc& m, HostTables& h) {
   if (m.kind != ED_HUBBARD || !m.spin_cut) {
@@ -280,11 +289,6 @@ ed_status host_tables(const ed_model_desc& m, HostTables& h) {
   };
   side(ha, c->A, bl.s, h.A_rp, h.A_col, h.A_val, h.A_diag, h.A_str);
   side(hb, c->B, bl.kB, h.B_rp, h.B_col, h.B_val, h.B_diag, h.B_str);
-  if (h.dA <= kBatchMaxDense) {
-    h.A_dense.assign(h.dA * h.dA, 0.f);
-    for (int64_t a = 0; a < h.dA; ++a)
-      for (int e = h.A_rp[a]; e < h.A_rp[a + 1]; ++e) h.A_dense[a * h.dA + h.A_col[e]] += h.A_val[e];
-  }
   h.c0 = (float)c->diag.c0;
   h.ncls = c->diag.ncls;
   h.vab_and = c->diag.vab_and;
@@ -295,16 +299,69 @@ ed_status host_tables(const ed_model_desc& m, HostTables& h) {
   return ED_OK;
 }
 
-size_t tables_bytes(const HostTables& h, int max_iter) {
+bool dense_capable(const HostTables& h) { return h.dA <= kBDenseMax && h.dB <= kBDenseMax; }
+
+// bytes of the CSR tables (uploaded), then of the dense form: the pieces of
+// H_A, H_B (uploaded) and of Psi, Psi^T (written by every apply)
+size_t csr_bytes(const HostTables& h) {
   size_t b = 0;
-  b += align256((size_t)3 * h.dA * h.dB * 4);
   b += align256(h.A_rp.size() * 4) + align256(h.A_col.size() * 4) + align256(h.A_val.size() * 4);
   b += align256(h.A_diag.size() * 4) + align256(h.A_str.size() * 4);
   b += align256(h.B_rp.size() * 4) + align256(h.B_col.size() * 4) + align256(h.B_val.size() * 4);
   b += align256(h.B_diag.size() * 4) + align256(h.B_str.size() * 4);
-  b += align256(h.A_dense.size() * 4);
-  (void)max_iter;
   return b;
+}
+// words of the nonzero-K-block masks: 128-row tiles of H_A, 64- and 128-row tiles of H_B
+size_t kmask_words(const HostTables& h) {
+  return (size_t)((h.dA + 127) / 128 + (h.dB + 63) / 64 + (h.dB + 127) / 128);
+}
+size_t h_piece_bytes(const HostTables& h) {
+  return align256((size_t)3 * h.dA * pad8(h.dA) * 2) + align256((size_t)3 * h.dB * pad8(h.dB) * 2) +
+         align256(kmask_words(h) * 4);
+}
+size_t x_piece_bytes(const HostTables& h) {
+  return align256((size_t)3 * h.dA * pad8(h.dB) * 2) + align256((size_t)3 * h.dB * pad8(h.dA) * 2);
+}
+size_t tables_bytes(const HostTables& h, bool dense) {
+  size_t b = align256((size_t)3 * h.dA * h.dB * 4) + csr_bytes(h);
+  if (dense && dense_capable(h)) b += h_piece_bytes(h) + x_piece_bytes(h);
+  return b;
+}
+
+// dense side operator (off-diagonal part, from the CSR) as three BF16 pieces
+// [3][d][pad8(d)]
+void side_pieces(const std::vector<int>& rp, const std::vector<int>& col, const std::vector<float>& val, int64_t d,
+                 std::vector<uint16_t>& out) {
+  const int kp = pad8(d);
+  std::vector<float> dense((size_t)d * kp, 0.f);
+  for (int64_t r = 0; r < d; ++r)
+    for (int e = rp[r]; e < rp[r + 1]; ++e) dense[(size_t)r * kp + col[e]] += val[e];
+  out.assign((size_t)3 * d * kp, 0);
+  const size_t plane = (size_t)d * kp;
+  for (size_t i = 0; i < plane; ++i) {
+    uint16_t h[3];
+    bf16_split3_host(dense[i], h);
+    out[i] = h[0];
+    out[plane + i] = h[1];
+    out[2 * plane + i] = h[2];
+  }
+}
+
+// chosen mode per instance shape, shared by every engine of the process
+using ShapeKey = std::array<long long, 4>;
+std::mutex g_mode_mu;
+std::map<ShapeKey, int> g_mode_cache;
+
+bool cached_mode(const long long* key, int* mode) {
+  std::lock_guard<std::mutex> lk(g_mode_mu);
+  auto it = g_mode_cache.find(ShapeKey{key[0], key[1], key[2], key[3]});
+  if (it == g_mode_cache.end()) return false;
+  *mode = it->second;
+  return true;
+}
+void cache_mode(const long long* key, int mode) {
+  std::lock_guard<std::mutex> lk(g_mode_mu);
+  g_mode_cache[ShapeKey{key[0], key[1], key[2], key[3]}] = mode;
 }
 }  // namespace
 
@@ -315,7 +372,7 @@ BatchEngine::~BatchEngine() {
   if (st_) cudaStreamDestroy(st_);
 }
 
-ed_status BatchEngine::init(int device, size_t arena_bytes, int max_slots, int max_iter) {
+ed_status BatchEngine::init(int device, size_t arena_bytes, int max_slots, int max_iter, bool dense) {
   device_ = device;
   ED_DEVICE_SCOPE(device);
   if (cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -323,8 +380,11 @@ ed_status BatchEngine::init(int device, size_t arena_bytes, int max_slots, int m
     sms_ = 148;
   }
   ED_CUDA_TRY(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+  dense_ = dense;
+  if (dense_) ED_TRY(bdense_prepare());
   max_slots_ = std::max(1, max_slots);
   max_iter_ = std::max(2, max_iter);
+  list_cap_ = max_slots_ + 4096;  // the tuner's replicated lists are longer than the slot count
   arena_bytes_ = align256(std::max<size_t>(arena_bytes, 1 << 20));
   auto get = [&](void** p, size_t bytes) -> ed_status {
     cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
@@ -340,10 +400,22 @@ ed_status BatchEngine::init(int device, size_t arena_bytes, int max_slots, int m
   free_.assign(1, {0, arena_bytes_});
   slots_.assign(max_slots_, BSlot{});
   ED_TRY(get((void**)&d_inst_, sizeof(BInst) * max_slots_));
+  ED_CUDA_TRY(cudaMemset(d_inst_, 0, sizeof(BInst) * max_slots_));
   ED_TRY(get((void**)&d_idx_, sizeof(int) * max_slots_));
-  ED_TRY(get((void**)&d_rowpref_, sizeof(long long) * (max_slots_ + 1)));
   ED_TRY(get((void**)&d_chunkpref_, sizeof(long long) * (max_slots_ + 1)));
   ED_TRY(get((void**)&d_nact_, sizeof(int) * 4));
+  ED_TRY(get((void**)&d_cnt_, sizeof(int) * 4));
+  ED_TRY(get((void**)&d_cidx_, sizeof(int) * list_cap_));
+  ED_TRY(get((void**)&d_crowpref_, sizeof(long long) * (list_cap_ + 1)));
+  ED_TRY(get((void**)&d_didx_, sizeof(int) * list_cap_));
+  ED_TRY(get((void**)&d_dspref_, sizeof(long long) * (list_cap_ + 1)));
+  ED_TRY(get((void**)&d_idx64_, sizeof(int) * list_cap_));
+  ED_TRY(get((void**)&d_tpref64_, sizeof(long long) * (list_cap_ + 1)));
+  ED_TRY(get((void**)&d_idx128_, sizeof(int) * list_cap_));
+  ED_TRY(get((void**)&d_tpref128_, sizeof(long long) * (list_cap_ + 1)));
+  ED_TRY(get((void**)&d_maps_, sizeof(CUtensorMap) * kBMaps * (size_t)max_slots_));
+  ED_TRY(get((void**)&d_err_, sizeof(int) * 4));
+  ED_CUDA_TRY(cudaMemset(d_err_, 0, sizeof(int) * 4));
   ED_TRY(get((void**)&d_it_, sizeof(int) * max_slots_));
   ED_TRY(get((void**)&d_alpha_, sizeof(double) * max_slots_));
   ED_TRY(get((void**)&d_beta_, sizeof(double) * max_slots_));
@@ -401,15 +473,18 @@ int BatchEngine::active_count() const {
   return n;
 }
 
-ed_status BatchEngine::instance_bytes(const ed_model_desc& m, int max_iter, size_t* bytes, int64_t* dim) {
+ed_status BatchEngine::instance_bytes(const ed_model_desc& m, bool dense, size_t* bytes, int64_t* dim) {
   HostTables h;
   ED_TRY(host_tables(m, h));
-  *bytes = tables_bytes(h, max_iter);
+  *bytes = tables_bytes(h, dense);
   if (dim) *dim = h.dA * h.dB;
   return ED_OK;
 }
 
 ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out) {
+  // the calling thread may be new to CUDA (the serving worker): make the
+  // device's context current for the tensor-map encoding (a driver call)
+  ED_DEVICE_SCOPE(device_);
   HostTables h;
   ED_TRY(host_tables(m, h));
   int slot = -1;
@@ -422,15 +497,19 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
     set_error("batch engine: no free slot");
     return ED_ENOMEM;
   }
-  const size_t need = tables_bytes(h, max_iter_);
+  const bool dn = dense_ && dense_capable(h);
+  const size_t need = tables_bytes(h, dense_);
   size_t off;
   if (!alloc(need, &off)) {
     set_error("batch engine: instance needs %zu bytes, %zu free", need, arena_free());
     return ED_ENOMEM;
   }
-  // lay the instance out in its arena range
-  std::vector<char> host(need, 0);
-  size_t cur = align256((size_t)3 * h.dA * h.dB * 4);
+  // lay the instance out in its arena range: three vectors, the CSR tables
+  // and the H pieces (uploaded together), the Psi pieces (scratch)
+  const size_t tab0 = align256((size_t)3 * h.dA * h.dB * 4);
+  const size_t up_end = tab0 + csr_bytes(h) + (dn ? h_piece_bytes(h) : 0);
+  std::vector<char> host(up_end, 0);
+  size_t cur = tab0;
   BSlot& S = slots_[slot];
   BInst& d = S.d;
   double* ha = d.hist_a;
@@ -440,7 +519,7 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
   d.hist_b = hb;
   auto put = [&](const void* src, size_t bytes) -> void* {
     void* dst = arena_ + off + cur;
-    if (bytes) std::memcpy(host.data() + cur, src, bytes);
+    if (bytes && src) std::memcpy(host.data() + cur, src, bytes);
     cur += align256(bytes);
     return dst;
   };
@@ -459,8 +538,6 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
   d.B_val = (const float*)put(h.B_val.data(), h.B_val.size() * 4);
   d.B_diag = (const float*)put(h.B_diag.data(), h.B_diag.size() * 4);
   d.B_str = (const uint32_t*)put(h.B_str.data(), h.B_str.size() * 4);
-  d.A_dense = h.A_dense.empty() ? nullptr : (const float*)put(h.A_dense.data(), h.A_dense.size() * 4);
-  d.use_dense = (d.A_dense && h.dA <= dense_threshold_) ? 1 : 0;
   d.c0 = h.c0;
   d.ncls = h.ncls;
   d.vab_and = h.vab_and;
@@ -468,13 +545,49 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
     d.w[q] = h.w[q];
     d.mask[q] = h.mask[q];
   }
-  const size_t tab0 = align256((size_t)3 * h.dA * h.dB * 4);
-  ED_CUDA_TRY(cudaMemcpyAsync(arena_ + off + tab0, host.data() + tab0, need - tab0, cudaMemcpyHostToDevice, st_));
+  S.key[0] = h.dA;
+  S.key[1] = h.dB;
+  S.key[2] = h.A_rp.back();
+  S.key[3] = h.B_rp.back();
+  d.mode = kModeCSR;
+  if (dn) {
+    std::vector<uint16_t> pa, pb;
+    side_pieces(h.A_rp, h.A_col, h.A_val, h.dA, pa);
+    side_pieces(h.B_rp, h.B_col, h.B_val, h.dB, pb);
+    d.KpA = pad8(h.dA);
+    d.KpB = pad8(h.dB);
+    d.HA = (const uint16_t*)put(pa.data(), pa.size() * 2);
+    d.HB = (const uint16_t*)put(pb.data(), pb.size() * 2);
+    std::vector<uint32_t> km(kmask_words(h), 0u);
+    const size_t tmA = (h.dA + 127) / 128, tn64 = (h.dB + 63) / 64;
+    for (int64_t r = 0; r < h.dA; ++r)
+      for (int e = h.A_rp[r]; e < h.A_rp[r + 1]; ++e) km[r / 128] |= 1u << (h.A_col[e] / 64);
+    for (int64_t r = 0; r < h.dB; ++r)
+      for (int e = h.B_rp[r]; e < h.B_rp[r + 1]; ++e) {
+        km[tmA + r / 64] |= 1u << (h.B_col[e] / 64);
+        km[tmA + tn64 + r / 128] |= 1u << (h.B_col[e] / 64);
+      }
+    d.kmask = (const uint32_t*)put(km.data(), km.size() * 4);
+    d.XN = (uint16_t*)put(nullptr, (size_t)3 * h.dA * d.KpB * 2);
+    d.XT = (uint16_t*)put(nullptr, (size_t)3 * h.dB * d.KpA * 2);
+    // A-role maps (H_A, Psi) with 128-row boxes; B-role maps (Psi^T, H_B)
+    // with 64- and 128-row boxes, one pair per output tile width
+    CUtensorMap mp[kBMaps];
+    ED_TRY(tmap_bf16_planes(&mp[0], d.HA, d.dA, d.dA, 3, d.KpA, 128));
+    ED_TRY(tmap_bf16_planes(&mp[1], d.XN, d.dB, d.dA, 3, d.KpB, 128));
+    ED_TRY(tmap_bf16_planes(&mp[2], d.XT, d.dA, d.dB, 3, d.KpA, 64));
+    ED_TRY(tmap_bf16_planes(&mp[3], d.HB, d.dB, d.dB, 3, d.KpB, 64));
+    ED_TRY(tmap_bf16_planes(&mp[4], d.XT, d.dA, d.dB, 3, d.KpA, 128));
+    ED_TRY(tmap_bf16_planes(&mp[5], d.HB, d.dB, d.dB, 3, d.KpB, 128));
+    ED_CUDA_TRY(cudaMemcpyAsync(d_maps_ + (size_t)slot * kBMaps, mp, sizeof(mp), cudaMemcpyHostToDevice, st_));
+  }
+  ED_CUDA_TRY(cudaMemcpyAsync(arena_ + off + tab0, host.data() + tab0, up_end - tab0, cudaMemcpyHostToDevice, st_));
   S.used = true;
   S.active = false;
   S.alloc_off = off;
   S.alloc_len = need;
-  S.has_dense = d.A_dense != nullptr;
+  S.dense_ok = dn ? 1 : 0;
+  d.mode = dn ? default_mode(S) : kModeCSR;
   ED_CUDA_TRY(cudaMemcpyAsync(d_inst_ + slot, &d, sizeof(BInst), cudaMemcpyHostToDevice, st_));
   ED_CUDA_TRY(cudaStreamSynchronize(st_));
   ED_TRY(restart(slot, seed));
@@ -511,27 +624,65 @@ void BatchEngine::remove(int slot) {
   rebuild_active();
 }
 
-ed_status BatchEngine::set_dense_threshold(int t) {
-  dense_threshold_ = t;
-  for (int s = 0; s < max_slots_; ++s) {
-    BSlot& S = slots_[s];
-    if (!S.used) continue;
-    S.d.use_dense = (S.has_dense && S.d.dA <= t) ? 1 : 0;
-    ED_CUDA_TRY(cudaMemcpyAsync(d_inst_ + s, &S.d, sizeof(BInst), cudaMemcpyHostToDevice, st_));
+ed_status BatchEngine::set_mode(int slot, int mode) {
+  BSlot& S = slots_[slot];
+  if (S.used) S.d.mode = S.dense_ok ? mode : kModeCSR;  // takes effect at the next rebuild_active
+  return ED_OK;
+}
+
+int BatchEngine::default_mode(const BSlot& S) const {
+  int md;
+  if (cached_mode(S.key, &md)) return md;
+  return S.d.dB <= 64 ? kModeD64 : kModeD128;
+}
+
+ed_status BatchEngine::upload_inst(int slot) {
+  ED_CUDA_TRY(cudaMemcpyAsync(d_inst_ + slot, &slots_[slot].d, sizeof(BInst), cudaMemcpyHostToDevice, st_));
+  ED_CUDA_TRY(cudaStreamSynchronize(st_));
+  return ED_OK;
+}
+
+ed_status BatchEngine::upload_lists(const std::vector<int>& csr, const std::vector<int>& d64,
+                                    const std::vector<int>& d128) {
+  if ((int)csr.size() > list_cap_ || (int)(d64.size() + d128.size()) > list_cap_) {
+    set_error("batch engine: work list exceeds capacity");
+    return ED_ENOMEM;
   }
+  std::vector<long long> crp(1, 0), sp(1, 0), tp64(1, 0), tp128(1, 0);
+  std::vector<int> dall(d64);
+  dall.insert(dall.end(), d128.begin(), d128.end());
+  for (int s : csr) crp.push_back(crp.back() + slots_[s].d.dA);
+  for (int s : dall) sp.push_back(sp.back() + (long long)((slots_[s].d.dA + 31) / 32) * ((slots_[s].d.dB + 31) / 32));
+  for (int s : d64) tp64.push_back(tp64.back() + (long long)((slots_[s].d.dA + 127) / 128) * ((slots_[s].d.dB + 63) / 64));
+  for (int s : d128)
+    tp128.push_back(tp128.back() + (long long)((slots_[s].d.dA + 127) / 128) * ((slots_[s].d.dB + 127) / 128));
+  auto up = [&](void* dst, const void* src, size_t bytes) -> ed_status {
+    if (bytes) ED_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st_));
+    return ED_OK;
+  };
+  ED_TRY(up(d_cidx_, csr.data(), csr.size() * 4));
+  ED_TRY(up(d_crowpref_, crp.data(), crp.size() * 8));
+  ED_TRY(up(d_didx_, dall.data(), dall.size() * 4));
+  ED_TRY(up(d_dspref_, sp.data(), sp.size() * 8));
+  ED_TRY(up(d_idx64_, d64.data(), d64.size() * 4));
+  ED_TRY(up(d_tpref64_, tp64.data(), tp64.size() * 8));
+  ED_TRY(up(d_idx128_, d128.data(), d128.size() * 4));
+  ED_TRY(up(d_tpref128_, tp128.data(), tp128.size() * 8));
+  const int cnt[4] = {(int)csr.size(), (int)dall.size(), (int)d64.size(), (int)d128.size()};
+  ED_TRY(up(d_cnt_, cnt, sizeof(cnt)));
   ED_CUDA_TRY(cudaStreamSynchronize(st_));
   return ED_OK;
 }
 
 ed_status BatchEngine::rebuild_active() {
-  std::vector<int> idx;
-  std::vector<long long> rp(1, 0), cp(1, 0);
+  std::vector<int> idx, csr, d64, d128;
+  std::vector<long long> cp(1, 0);
   for (int s = 0; s < max_slots_; ++s) {
     const BSlot& S = slots_[s];
     if (!S.used || !S.active) continue;
     idx.push_back(s);
-    rp.push_back(rp.back() + S.d.dA);
     cp.push_back(cp.back() + (S.d.D + kBatchChunk - 1) / kBatchChunk);
+    (S.d.mode == kModeD64 ? d64 : S.d.mode == kModeD128 ? d128 : csr).push_back(s);
   }
   if (cp.back() > part_cap_) {
     set_error("batch engine: reduction chunks exceed capacity");
@@ -539,18 +690,41 @@ ed_status BatchEngine::rebuild_active() {
   }
   int n = (int)idx.size();
   if (!idx.empty()) ED_CUDA_TRY(cudaMemcpyAsync(d_idx_, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, st_));
-  ED_CUDA_TRY(cudaMemcpyAsync(d_rowpref_, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice, st_));
   ED_CUDA_TRY(cudaMemcpyAsync(d_chunkpref_, cp.data(), cp.size() * 8, cudaMemcpyHostToDevice, st_));
   ED_CUDA_TRY(cudaMemcpyAsync(d_nact_, &n, 4, cudaMemcpyHostToDevice, st_));
-  ED_CUDA_TRY(cudaStreamSynchronize(st_));
+  return upload_lists(csr, d64, d128);
+}
+
+ed_status BatchEngine::launch_apply(cudaStream_t s, const float* x, float* y) {
+  const int user = x != nullptr;
+  if (dense_) {
+    BDenseArgs a;
+    a.insts = d_inst_;
+    a.cnt = d_cnt_;
+    a.didx = d_didx_;
+    a.dspref = d_dspref_;
+    a.idx64 = d_idx64_;
+    a.tpref64 = d_tpref64_;
+    a.idx128 = d_idx128_;
+    a.tpref128 = d_tpref128_;
+    a.maps = d_maps_;
+    a.ux = x;
+    a.uy = y;
+    a.arena = (float*)arena_;
+    a.user_mode = user;
+    a.sms = sms_;
+    a.err = d_err_;
+    ED_TRY(bdense_apply(a, s));
+  }
+  k_bapply<<<sms_ * 4, 256, 0, s>>>(d_inst_, d_cidx_, d_crowpref_, d_cnt_, x, y, (float*)arena_, user);
+  ED_CUDA_TRY(cudaGetLastError());
   return ED_OK;
 }
 
 ed_status BatchEngine::launch_step(cudaStream_t s) {
   float* arena_f = (float*)arena_;
-  const int g_apply = sms_ * 4;
   const int g_red = sms_ * 4;
-  k_bapply<<<g_apply, 256, 0, s>>>(d_inst_, d_idx_, d_rowpref_, d_nact_, nullptr, nullptr, arena_f, 0);
+  ED_TRY(launch_apply(s, nullptr, nullptr));
   k_blz_a<<<g_red, 256, 0, s>>>(d_inst_, d_idx_, d_chunkpref_, d_nact_, arena_f, d_beta_, d_part_);
   k_bfin<<<(max_slots_ * 32 + 255) / 256, 256, 0, s>>>(d_inst_, d_idx_, d_chunkpref_, d_nact_, d_part_, d_alpha_, d_it_,
                                                      max_iter_, 0);
@@ -560,6 +734,90 @@ ed_status BatchEngine::launch_step(cudaStream_t s) {
   k_blz_c<<<g_red, 256, 0, s>>>(d_inst_, d_idx_, d_chunkpref_, d_nact_, arena_f, d_beta_);
   k_bstep<<<(max_slots_ + 255) / 256, 256, 0, s>>>(d_idx_, d_nact_, d_it_);
   return ED_OK;
+}
+
+ed_status BatchEngine::time_apply(int reps, float* ms) {
+  cudaEvent_t e0, e1;
+  ED_CUDA_TRY(cudaEventCreate(&e0));
+  ED_CUDA_TRY(cudaEventCreate(&e1));
+  ed_status st = launch_apply(st_, nullptr, nullptr);  // warm
+  if (st == ED_OK) {
+    cudaEventRecord(e0, st_);
+    for (int i = 0; i < reps && st == ED_OK; ++i) st = launch_apply(st_, nullptr, nullptr);
+    cudaEventRecord(e1, st_);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / (float)std::max(1, reps);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+// Modes of a set of instances (normally the whole batch) chosen on the
+// batch itself: start from the dense form everywhere it exists (64-wide
+// tiles when d_B <= 64, else 128-wide), then, for classes of instances of
+// similar size (D in [4^k, 4^(k+1))), largest total first, try each other
+// mode for the whole class and keep it when the timed batched H psi gets
+// at least 1 % faster.  Timing the real mix accounts for what a shape timed
+// alone would not: cache sharing between instances and the split of the
+// apply into the CSR and dense launches.  Each shape's choice is cached
+// for later engines of the process (the serving loop's admissions).
+ed_status BatchEngine::tune(const std::vector<int>& slots) {
+  ED_DEVICE_SCOPE(device_);
+  std::map<int, std::vector<int>> cls;  // size class -> dense-capable slots
+  for (int s : slots) {
+    BSlot& S = slots_[s];
+    if (!S.used) continue;
+    S.d.mode = S.dense_ok ? default_mode(S) : kModeCSR;
+    if (!S.dense_ok) continue;
+    int k = 0;
+    for (long long D = S.d.D; D >= 4; D >>= 2) ++k;
+    cls[k].push_back(s);
+  }
+  std::vector<std::pair<long long, int>> order;
+  for (auto& kv : cls) {
+    long long tot = 0;
+    for (int s : kv.second) tot += slots_[s].d.D;
+    order.push_back({-tot, kv.first});
+  }
+  std::sort(order.begin(), order.end());
+  ED_TRY(rebuild_active());
+  float best = 0.f;
+  ED_TRY(time_apply(5, &best));
+  for (auto& o : order) {
+    std::vector<int>& g = cls[o.second];
+    std::vector<int> keep(g.size());
+    for (size_t i = 0; i < g.size(); ++i) keep[i] = slots_[g[i]].d.mode;
+    for (int m : {kModeCSR, kModeD64, kModeD128}) {
+      bool same = true;
+      for (int s : g) same = same && slots_[s].d.mode == m;
+      if (same) continue;
+      std::vector<int> prev(g.size());
+      for (size_t i = 0; i < g.size(); ++i) {
+        prev[i] = slots_[g[i]].d.mode;
+        slots_[g[i]].d.mode = m;
+      }
+      ED_TRY(rebuild_active());
+      float t = 0.f;
+      ED_TRY(time_apply(5, &t));
+      if (t < 0.99f * best) {
+        best = t;
+      } else {
+        for (size_t i = 0; i < g.size(); ++i) slots_[g[i]].d.mode = prev[i];
+      }
+    }
+  }
+  for (int s : slots)
+    if (slots_[s].used && slots_[s].dense_ok) cache_mode(slots_[s].key, slots_[s].d.mode);
+  int err = 0;
+  ED_CUDA_TRY(cudaMemcpy(&err, d_err_, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    set_error("batch engine: a tensor-core wait ran out while tuning");
+    return ED_ETIMEOUT;
+  }
+  return rebuild_active();
 }
 
 ed_status BatchEngine::capture() {
@@ -580,13 +838,17 @@ ed_status BatchEngine::steps(int k) {
 }
 
 ed_status BatchEngine::apply_user(const float* x, float* y, cudaStream_t st) {
-  k_bapply<<<sms_ * 4, 256, 0, st>>>(d_inst_, d_idx_, d_rowpref_, d_nact_, x, y, (float*)arena_, 1);
-  ED_CUDA_TRY(cudaGetLastError());
-  return ED_OK;
+  return launch_apply(st, x, y);
 }
 
 ed_status BatchEngine::sync() {
   ED_CUDA_TRY(cudaStreamSynchronize(st_));
+  int err = 0;
+  ED_CUDA_TRY(cudaMemcpy(&err, d_err_, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    set_error("batch engine: a tensor-core wait ran out; results are incomplete");
+    return ED_ETIMEOUT;
+  }
   return ED_OK;
 }
 
@@ -601,7 +863,13 @@ ed_status BatchEngine::poll(double tol, int every, std::vector<int>* done) {
   ED_CUDA_TRY(cudaMemcpyAsync(it.data(), d_it_, sizeof(int) * max_slots_, cudaMemcpyDeviceToHost, st_));
   ED_CUDA_TRY(cudaMemcpyAsync(hist_host_.data(), d_hist_, sizeof(double) * hist_host_.size(), cudaMemcpyDeviceToHost,
                               st_));
+  int err = 0;
+  ED_CUDA_TRY(cudaMemcpyAsync(&err, d_err_, sizeof(int), cudaMemcpyDeviceToHost, st_));
   ED_CUDA_TRY(cudaStreamSynchronize(st_));
+  if (err) {
+    set_error("batch engine: a tensor-core wait ran out; the Lanczos state is invalid");
+    return ED_ETIMEOUT;
+  }
   bool changed = false;
   for (int s = 0; s < max_slots_; ++s) {
     BSlot& S = slots_[s];

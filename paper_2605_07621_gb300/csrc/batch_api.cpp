@@ -1,7 +1,7 @@
 // Batched form: many independent Hubbard instances (spin-up|spin-down cut)
 // in one persistent launch per kernel with a captured Lanczos-step graph;
-// the per-instance choice between a CSR and a dense H_A is autotuned by
-// timing the batched apply.
+// the per-instance choice between the CSR apply and the dense tensor-core
+// apply (and its output tile width) is autotuned per instance shape.
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -16,29 +16,36 @@ struct ed_batch {
   std::vector<int> slot;
   std::vector<int64_t> off;
   int n = 0;
-  int threshold = 0;
-  float tune_ms[5] = {0, 0, 0, 0, 0};
+  float tune_ms[4] = {0, 0, 0, 0};
 };
 
-static const int kThresholds[5] = {0, 8, 16, 32, 64};
 static const int kBatchHist = 1024;
+
+// whole-batch apply (ms) with every instance in `mode` (dense modes only
+// where the instance has the dense form)
+static ed_status time_uniform(ed_batch* B, int mode, float* ms) {
+  for (int i = 0; i < B->n; ++i) ED_TRY(B->eng.set_mode(B->slot[i], mode));
+  ED_TRY(B->eng.rebuild_active());
+  return B->eng.time_apply(3, ms);
+}
 
 extern "C" ed_status ed_batch_create(const ed_model_desc* models, int n, int flags, ed_batch** out) {
   if (!out || !models || n < 1) { set_error("ed_batch_create: bad arguments"); return ED_EINVAL; }
   if (flags < 0 || flags > 2) { set_error("bad flags %d", flags); return ED_EINVAL; }
   *out = nullptr;
+  const bool dense = flags != ED_OPS_FORCE_CSR;
   size_t total = 0;
   std::vector<int64_t> dims(n);
   for (int i = 0; i < n; ++i) {
     size_t b;
-    ED_TRY(BatchEngine::instance_bytes(models[i], kBatchHist, &b, &dims[i]));
+    ED_TRY(BatchEngine::instance_bytes(models[i], dense, &b, &dims[i]));
     total += b + 512;
   }
   ed_batch* B = new (std::nothrow) ed_batch();
   if (!B) { set_error("host allocation failed"); return ED_ENOMEM; }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
-  ed_status st = B->eng.init(dev, total + (1 << 20), n, kBatchHist);
+  ed_status st = B->eng.init(dev, total + (1 << 20), n, kBatchHist, dense);
   if (st != ED_OK) { delete B; return st; }
   B->n = n;
   B->slot.resize(n);
@@ -49,37 +56,25 @@ extern "C" ed_status ed_batch_create(const ed_model_desc* models, int n, int fla
     B->off[i + 1] = B->off[i] + dims[i];
     BSlot& S = B->eng.slots()[B->slot[i]];
     S.d.uoff = B->off[i];
-  }
-  // descriptors with user offsets and the dense threshold
-  int thr = (flags & 3) == ED_OPS_FORCE_CSR ? 0 : (flags & 3) == ED_OPS_FORCE_DENSE ? kBatchMaxDense : 16;
-  st = B->eng.set_dense_threshold(thr);
-  if (st != ED_OK) { delete B; return st; }
-  if (flags == ED_OPS_DEFAULT) {
-    // autotune: time the batched apply for each dense threshold
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_t = 0;
-    for (int k = 0; k < 5; ++k) {
-      B->eng.set_dense_threshold(kThresholds[k]);
-      B->eng.steps(1);  // warm
-      cudaEventRecord(e0, B->eng.stream());
-      B->eng.steps(3);
-      cudaEventRecord(e1, B->eng.stream());
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      B->tune_ms[k] = ms / 3.f;
-      if (ms < best) { best = ms; best_t = kThresholds[k]; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    thr = best_t;
-    st = B->eng.set_dense_threshold(thr);
+    st = B->eng.upload_inst(B->slot[i]);
     if (st != ED_OK) { delete B; return st; }
   }
-  B->threshold = thr;
+  if (flags == ED_OPS_DEFAULT) {
+    // the batch with every instance in each mode, then the tuned choice
+    for (int k = 0; k < 3 && st == ED_OK; ++k) st = time_uniform(B, k, &B->tune_ms[k]);
+    if (st == ED_OK) st = B->eng.tune(B->slot);
+    if (st == ED_OK) st = B->eng.time_apply(3, &B->tune_ms[3]);
+  } else {
+    if (flags == ED_OPS_FORCE_DENSE)
+      for (int i = 0; i < n && st == ED_OK; ++i) {
+        const BSlot& S = B->eng.slots()[B->slot[i]];
+        st = B->eng.set_mode(B->slot[i], S.d.dB <= 64 ? kModeD64 : kModeD128);
+      }
+    if (st == ED_OK) st = B->eng.rebuild_active();
+    if (st == ED_OK) st = B->eng.time_apply(3, &B->tune_ms[3]);
+  }
+  if (st == ED_OK) st = B->eng.sync();
+  if (st != ED_OK) { delete B; return st; }
   *out = B;
   return ED_OK;
 }
@@ -92,16 +87,16 @@ extern "C" ed_status ed_batch_offsets(const ed_batch* b, int64_t* off) {
   return ED_OK;
 }
 
-extern "C" ed_status ed_batch_info(const ed_batch* b, int* dense_threshold, float* tune_ms) {
+extern "C" ed_status ed_batch_info(const ed_batch* b, int* modes, float* tune_ms) {
   if (!b) { set_error("NULL batch"); return ED_EINVAL; }
-  if (dense_threshold) *dense_threshold = b->threshold;
+  if (modes)
+    for (int i = 0; i < b->n; ++i) modes[i] = b->eng.mode(b->slot[i]);
   if (tune_ms) std::memcpy(tune_ms, b->tune_ms, sizeof(b->tune_ms));
   return ED_OK;
 }
 
 static ed_status activate_all(ed_batch* b) {
   for (int i = 0; i < b->n; ++i) b->eng.slots()[b->slot[i]].active = true;
-  ED_TRY(b->eng.set_dense_threshold(b->threshold));
   return b->eng.rebuild_active();
 }
 
@@ -125,7 +120,6 @@ extern "C" ed_status ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, 
   const int max_iter = std::min(o.max_iter, b->eng.max_iter());
   const int K = std::max(1, o.check_every);
   for (int i = 0; i < b->n; ++i) ED_TRY(b->eng.restart(b->slot[i], o.seed));
-  ED_TRY(b->eng.set_dense_threshold(b->threshold));
   int steps = 0;
   while (b->eng.active_count() > 0 && steps < max_iter) {
     const int k = std::min(K, max_iter - steps);

@@ -104,26 +104,34 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over the digit planes: (K, R, 8) BF16, box (64, box_rows, 1),
-// 128-byte swizzle, out-of-range elements read as zero
-static ed_status make_map(OzContext* o, OzOperand* op, int box_rows) {
+ed_status tmap_bf16_planes(CUtensorMap* m, const void* base, int K, int R, int planes, long long Kpad, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return ED_ECUDA;
   }
-  CUtensorMap m;
-  const cuuint64_t dims[3] = {(cuuint64_t)op->K, (cuuint64_t)op->R, (cuuint64_t)kOzDigits};
-  const cuuint64_t strides[2] = {(cuuint64_t)op->Kpad * 2, (cuuint64_t)op->Kpad * 2 * (cuuint64_t)op->R};
+  // a driver call: the calling thread needs a current context, which the
+  // runtime binds on its first call that needs one (cudaFree(0) is such a call)
+  cudaFree(nullptr);
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)Kpad * 2 * (cuuint64_t)R};
   const cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op->slices, dims, strides, box, estr,
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d operand", (int)r, op->R, op->K);
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d operand", (int)r, R, K);
     return ED_ECUDA;
   }
+  return ED_OK;
+}
+
+// 3-D map over the digit planes: (K, R, 8) BF16, box (64, box_rows, 1),
+// 128-byte swizzle, out-of-range elements read as zero
+static ed_status make_map(OzContext* o, OzOperand* op, int box_rows) {
+  CUtensorMap m;
+  ED_TRY(tmap_bf16_planes(&m, op->slices, op->K, op->R, kOzDigits, op->Kpad, box_rows));
   op->map = (int)o->maps.size();
   o->maps.push_back(m);
   return ED_OK;

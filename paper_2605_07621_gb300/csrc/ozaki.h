@@ -63,6 +63,10 @@ struct OzContext {
 };
 
 ed_status oz_alloc(OzContext* o, void** p, size_t bytes);
+// 3-D BF16 tensor map over `planes` planes of an R x K matrix (row stride
+// Kpad elements, a multiple of 8; planes one after another), box
+// (64, box_rows, 1), 128-byte swizzle, elements outside the matrix read as 0
+ed_status tmap_bf16_planes(CUtensorMap* m, const void* base, int K, int R, int planes, long long Kpad, int box_rows);
 // operand from a host FP64 row-major matrix (digits formed on the host)
 ed_status oz_operand_host(OzContext* o, const double* h, int R, int K, bool a_role, OzOperand* out);
 // operand buffers filled on the device by oz_slice_* (no data yet)

@@ -13,6 +13,7 @@
 #include <deque>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <unordered_map>
 
@@ -33,6 +34,7 @@ struct Request {
   int slot = -1;
   int state = 0;  // 0 queued, 1 running, 2 done, 3 cancelled, 4 failed
   ed_status status = ED_OK;
+  std::string msg;  // error text of a failed request (set on the worker thread)
   Clock::time_point t_submit, t_admit, t_done;
   double e0 = 0.0;
   int iterations = 0;
@@ -103,11 +105,14 @@ static void worker_loop(ed_server* S) {
         }
         int slot = -1;
         lk.unlock();
+        // CSR or tensor-core form: the choice cached for the shape by a
+        // tuned batch of this process, else the dense form
         ed_status st = S->eng.add(r.m, S->opts.seed, &slot);
         lk.lock();
         if (st != ED_OK) {
           r.state = 4;
           r.status = st;
+          r.msg = ed_last_error();
           r.t_done = Clock::now();
           ++S->failed;
           S->cv_done.notify_all();
@@ -132,10 +137,12 @@ static void worker_loop(ed_server* S) {
     std::lock_guard<std::mutex> lk(S->mu);
     if (st != ED_OK) {
       // device error: fail every running request and stop serving
+      const std::string msg = ed_last_error();
       for (auto& kv : S->reqs)
         if (kv.second.state == 1) {
           kv.second.state = 4;
           kv.second.status = st;
+          kv.second.msg = msg;
           kv.second.t_done = Clock::now();
           ++S->failed;
         }
@@ -189,7 +196,7 @@ extern "C" ed_status ed_server_create(const ed_server_opts* opts, ed_server** ou
   S->inject_left = o.inject_alloc_failures;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
-  ed_status st = S->eng.init(dev, (size_t)o.device_bytes, o.max_slots, o.max_iter);
+  ed_status st = S->eng.init(dev, (size_t)o.device_bytes, o.max_slots, o.max_iter, true);
   if (st != ED_OK) { delete S; return st; }
   S->free_cache = (int64_t)S->eng.arena_free();
   S->worker = std::thread(worker_loop, S);
@@ -201,7 +208,7 @@ extern "C" ed_status ed_server_submit(ed_server* S, const ed_model_desc* m, uint
   if (!S || !m || !ticket) { set_error("NULL argument"); return ED_EINVAL; }
   size_t bytes = 0;
   int64_t dim = 0;
-  ED_TRY(BatchEngine::instance_bytes(*m, S->opts.max_iter, &bytes, &dim));
+  ED_TRY(BatchEngine::instance_bytes(*m, true, &bytes, &dim));
   Request r;
   r.bi.assign(m->bi, m->bi + m->n_bonds);
   r.bj.assign(m->bj, m->bj + m->n_bonds);
@@ -252,6 +259,7 @@ extern "C" ed_status ed_server_wait(ed_server* S, uint64_t ticket, int timeout_m
   res->iterations = r.iterations;
   res->converged = r.converged;
   res->status = r.status;
+  if (r.status != ED_OK && r.status != ED_ENOCONV && !r.msg.empty()) set_error("%s", r.msg.c_str());
   res->latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
   if (r.state == 2 || (r.state == 3 && r.t_admit.time_since_epoch().count() != 0)) {
     res->queue_s = std::chrono::duration<double>(r.t_admit - r.t_submit).count();

@@ -398,10 +398,14 @@ class Batch:
         return off
 
     def info(self):
-        thr = ctypes.c_int()
-        ms = np.zeros(5, np.float32)
-        L.check(L.load().ed_batch_info(self._h, ctypes.byref(thr), ms.ctypes.data))
-        return thr.value, ms
+        """(modes, tune_ms): each instance's H psi mode (0 CSR, 1 dense on the
+        tensor cores with 64-column tiles, 2 with 128-column tiles) and the
+        batched apply's device time in ms with every instance in mode 0, 1,
+        2 and with the chosen modes."""
+        modes = np.zeros(len(self.models), np.int32)
+        ms = np.zeros(4, np.float32)
+        L.check(L.load().ed_batch_info(self._h, modes.ctypes.data, ms.ctypes.data))
+        return modes, ms
 
 
 def batch_create(models, flags: int = 0) -> Batch:

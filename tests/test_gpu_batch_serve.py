@@ -40,11 +40,10 @@ def _instances(n=24, max_dim=60000, seed=20260507):
     return out
 
 
-def test_batch_apply_parity(ed, oracle_mod):
+def _apply_vs_oracle(ed, oracle_mod, ms, flags):
     import torch
 
-    ms = _instances(24)
-    b = ed.batch_create(ms)
+    b = ed.batch_create(ms, flags=flags)
     off = b.offsets()
     x = np.zeros(b.dim)
     refs = []
@@ -59,20 +58,57 @@ def test_batch_apply_parity(ed, oracle_mod):
     ed.batch_apply(b, xt, yt)
     torch.cuda.synchronize()
     y = yt.double().cpu().numpy()
+    modes, _ = b.info()
     for i in range(len(ms)):
         r = refs[i]
         err = np.linalg.norm(y[off[i]:off[i + 1]] - r) / np.linalg.norm(r)
-        assert err <= 1e-6, (i, ms[i].name, err)
+        assert err <= 1e-6, (i, ms[i].name, int(modes[i]), err)
+    return modes
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_batch_apply_parity(ed, oracle_mod, flags):
+    """CSR (flags 1), dense tensor-core (flags 2) and tuned (0) applies
+    against the oracle on 24 instances of up to 60,000 states."""
+    modes = _apply_vs_oracle(ed, oracle_mod, _instances(24), flags)
+    if flags == 1:
+        assert (modes == 0).all()
+    if flags == 2:
+        assert (modes > 0).all()
+
+
+def _largest(n):
+    from math import comb
+
+    ms = W.batched_hubbard_instances(512, 20260507)
+    ms.sort(key=lambda m: -comb(m.n_sites, m.n_up) * comb(m.n_sites, m.n_dw))
+    return ms[:n]
+
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_batch_apply_parity_largest(ed, oracle_mod, flags):
+    """The largest instances (d_A, d_B up to 924: 15 output-tile rows of K
+    steps, ragged tiles in both directions) in CSR and dense form."""
+    ms = _largest(3) + [m for m in _instances(60) if min(m.n_up, m.n_dw) == 1][:2]
+    modes = _apply_vs_oracle(ed, oracle_mod, ms, flags)
+    if flags == 2:
+        assert (modes > 0).all()
+        assert set(modes.tolist()) == {1, 2}
 
 
 @pytest.mark.parametrize("flags", [0, 1, 2])
 def test_batch_lanczos_vs_oracle(ed, oracle_mod, flags):
     ms = _instances(16, max_dim=8000)
     b = ed.batch_create(ms, flags=flags)
-    thr, tune = b.info()
-    assert thr in (0, 8, 16, 32, 64)
+    modes, tune = b.info()
+    assert set(modes.tolist()) <= {0, 1, 2}
+    assert tune[3] > 0
     if flags == 0:
         assert (tune > 0).all()
+    if flags == 1:
+        assert (modes == 0).all()
+    if flags == 2:
+        assert (modes > 0).all()
     e, it, info = ed.batch_lanczos(b, tol=1e-7)
     assert info["all_converged"]
     for i, m in enumerate(ms):
