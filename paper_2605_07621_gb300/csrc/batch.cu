@@ -248,7 +248,9 @@ struct HostTables {
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-int pad8(int64_t d) { return (int)((d + 7) / 8 * 8); }
+// row stride of the BF16 pieces: 64 elements (128 bytes), so every row a
+// TMA box reads starts on a 128-byte line
+int pad64(int64_t d) { return (int)((d + 63) / 64 * 64); }
 
 ed_status host_tables(const ed_model_desc& m, HostTables& h) {
   if (m.kind != ED_HUBBARD || !m.spin_cut) {
@@ -316,11 +318,11 @@ size_t kmask_words(const HostTables& h) {
   return (size_t)((h.dA + 127) / 128 + (h.dB + 63) / 64 + (h.dB + 127) / 128);
 }
 size_t h_piece_bytes(const HostTables& h) {
-  return align256((size_t)3 * h.dA * pad8(h.dA) * 2) + align256((size_t)3 * h.dB * pad8(h.dB) * 2) +
+  return align256((size_t)3 * h.dA * pad64(h.dA) * 2) + align256((size_t)3 * h.dB * pad64(h.dB) * 2) +
          align256(kmask_words(h) * 4);
 }
 size_t x_piece_bytes(const HostTables& h) {
-  return align256((size_t)3 * h.dA * pad8(h.dB) * 2) + align256((size_t)3 * h.dB * pad8(h.dA) * 2);
+  return align256((size_t)3 * h.dA * pad64(h.dB) * 2) + align256((size_t)3 * h.dB * pad64(h.dA) * 2);
 }
 size_t tables_bytes(const HostTables& h, bool dense) {
   size_t b = align256((size_t)3 * h.dA * h.dB * 4) + csr_bytes(h);
@@ -329,10 +331,10 @@ size_t tables_bytes(const HostTables& h, bool dense) {
 }
 
 // dense side operator (off-diagonal part, from the CSR) as three BF16 pieces
-// [3][d][pad8(d)]
+// [3][d][pad64(d)]
 void side_pieces(const std::vector<int>& rp, const std::vector<int>& col, const std::vector<float>& val, int64_t d,
                  std::vector<uint16_t>& out) {
-  const int kp = pad8(d);
+  const int kp = pad64(d);
   std::vector<float> dense((size_t)d * kp, 0.f);
   for (int64_t r = 0; r < d; ++r)
     for (int e = rp[r]; e < rp[r + 1]; ++e) dense[(size_t)r * kp + col[e]] += val[e];
@@ -554,8 +556,8 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
     std::vector<uint16_t> pa, pb;
     side_pieces(h.A_rp, h.A_col, h.A_val, h.dA, pa);
     side_pieces(h.B_rp, h.B_col, h.B_val, h.dB, pb);
-    d.KpA = pad8(h.dA);
-    d.KpB = pad8(h.dB);
+    d.KpA = pad64(h.dA);
+    d.KpB = pad64(h.dB);
     d.HA = (const uint16_t*)put(pa.data(), pa.size() * 2);
     d.HB = (const uint16_t*)put(pb.data(), pb.size() * 2);
     std::vector<uint32_t> km(kmask_words(h), 0u);
@@ -652,7 +654,7 @@ ed_status BatchEngine::upload_lists(const std::vector<int>& csr, const std::vect
   std::vector<int> dall(d64);
   dall.insert(dall.end(), d128.begin(), d128.end());
   for (int s : csr) crp.push_back(crp.back() + slots_[s].d.dA);
-  for (int s : dall) sp.push_back(sp.back() + (long long)((slots_[s].d.dA + 31) / 32) * ((slots_[s].d.dB + 31) / 32));
+  for (int s : dall) sp.push_back(sp.back() + (long long)((slots_[s].d.dA + 63) / 64) * ((slots_[s].d.dB + 63) / 64));
   for (int s : d64) tp64.push_back(tp64.back() + (long long)((slots_[s].d.dA + 127) / 128) * ((slots_[s].d.dB + 63) / 64));
   for (int s : d128)
     tp128.push_back(tp128.back() + (long long)((slots_[s].d.dA + 127) / 128) * ((slots_[s].d.dB + 127) / 128));

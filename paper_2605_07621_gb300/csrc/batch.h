@@ -46,7 +46,7 @@ struct BInst {
   const uint16_t* HB;
   uint16_t* XN;
   uint16_t* XT;
-  int KpA, KpB;        // row strides of the pieces (d rounded up to 8)
+  int KpA, KpB;        // row strides of the pieces (d rounded up to 64)
   // nonzero 64-wide K blocks (bit kb) of each 128-row tile of H_A, then of
   // each 64-row and each 128-row tile of H_B: the dense products skip zero blocks
   const uint32_t* kmask;
@@ -64,7 +64,7 @@ struct BInst {
 struct BDenseArgs {
   const BInst* insts;
   const int* cnt;            // {CSR, dense, 64-wide, 128-wide} list lengths
-  const int* didx;           // dense slots, with their 32 x 32 slicing tiles
+  const int* didx;           // dense slots, with their 64 x 64 slicing tiles
   const long long* dspref;
   const int* idx64;          // slots with 128 x 64 output tiles
   const long long* tpref64;
@@ -174,7 +174,7 @@ class BatchEngine {
   int* d_cidx_ = nullptr;
   long long* d_crowpref_ = nullptr;
   int* d_didx_ = nullptr;
-  long long* d_dspref_ = nullptr;    // 32 x 32 slicing tiles
+  long long* d_dspref_ = nullptr;    // 64 x 64 slicing tiles
   int* d_idx64_ = nullptr;
   long long* d_tpref64_ = nullptr;
   int* d_idx128_ = nullptr;

@@ -91,46 +91,56 @@ __device__ __forceinline__ void split3_dev(float v, uint16_t& h0, uint16_t& h1, 
 }
 
 // Pieces of Psi (rows a, K = b) and of Psi^T (rows b, K = a) for every dense
-// instance: 32 x 32 tiles through shared memory so both stores coalesce.
+// instance: 64 x 64 tiles of Psi through shared memory; every warp store
+// writes 32 pairs of BF16 (128 bytes) along a row of either layout.  The
+// piece rows start on multiples of 64 elements, so pairs at even columns
+// are 4-byte aligned.
 __global__ void __launch_bounds__(256) k_bslice(BDenseArgs g) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[64][65];
   const int n = g.cnt[1];
   if (n <= 0) return;
   const long long total = g.dspref[n];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (long long u = blockIdx.x; u < total; u += gridDim.x) {
     const int ai = find_pref(g.dspref, n, u);
     const BInst& I = g.insts[g.didx[ai]];
     const int dA = I.dA, dB = I.dB;
     const long long t = u - g.dspref[ai];
-    const int tnb = (dB + 31) >> 5;
-    const int a0 = (int)(t / tnb) * 32, b0 = (int)(t % tnb) * 32;
-    const float* x = g.user_mode ? g.ux + I.uoff : g.arena + I.voff + I.D;
+    const int tnb = (dB + 63) >> 6;
+    const int a0 = (int)(t / tnb) * 64, b0 = (int)(t % tnb) * 64;
+    const float* __restrict__ x = g.user_mode ? g.ux + I.uoff : g.arena + I.voff + I.D;
+    uint16_t* __restrict__ XN = I.XN;
+    uint16_t* __restrict__ XT = I.XT;
     const long long pn = (long long)dA * I.KpB, pt = (long long)dB * I.KpA;
-    for (int j = ty; j < 32; j += 8) {
-      const int a = a0 + j, b = b0 + tx;
-      float v = 0.f;
-      if (a < dA && b < dB) {
-        v = x[(long long)a * dB + b];
-        uint16_t h0, h1, h2;
-        split3_dev(v, h0, h1, h2);
-        uint16_t* d = I.XN + (long long)a * I.KpB + b;
-        d[0] = h0;
-        d[pn] = h1;
-        d[2 * pn] = h2;
-      }
-      tile[j][tx] = v;
+    for (int i = threadIdx.x; i < 64 * 64; i += 256) {
+      const int r = i >> 6, c = i & 63;
+      const int a = a0 + r, b = b0 + c;
+      tile[r][c] = (a < dA && b < dB) ? x[(long long)a * dB + b] : 0.f;
     }
     __syncthreads();
-    for (int j = ty; j < 32; j += 8) {
-      const int b = b0 + j, a = a0 + tx;
+    const int c = 2 * lane;
+    for (int r = warp; r < 64; r += 8) {
+      const int a = a0 + r, b = b0 + c;  // Psi row a, columns b, b + 1
       if (a < dA && b < dB) {
-        uint16_t h0, h1, h2;
-        split3_dev(tile[tx][j], h0, h1, h2);
-        uint16_t* d = I.XT + (long long)b * I.KpA + a;
-        d[0] = h0;
-        d[pt] = h1;
-        d[2 * pt] = h2;
+        uint16_t h0, h1, h2, k0, k1, k2;
+        split3_dev(tile[r][c], h0, h1, h2);
+        split3_dev(tile[r][c + 1], k0, k1, k2);  // zero past d_B: the padding of the row
+        uint32_t* d = reinterpret_cast<uint32_t*>(XN + (long long)a * I.KpB + b);
+        d[0] = h0 | ((uint32_t)k0 << 16);
+        d[pn / 2] = h1 | ((uint32_t)k1 << 16);
+        d[pn] = h2 | ((uint32_t)k2 << 16);
+      }
+    }
+    for (int r = warp; r < 64; r += 8) {
+      const int b = b0 + r, a = a0 + c;  // Psi^T row b, columns a, a + 1
+      if (a < dA && b < dB) {
+        uint16_t h0, h1, h2, k0, k1, k2;
+        split3_dev(tile[c][r], h0, h1, h2);
+        split3_dev(tile[c + 1][r], k0, k1, k2);
+        uint32_t* d = reinterpret_cast<uint32_t*>(XT + (long long)b * I.KpA + a);
+        d[0] = h0 | ((uint32_t)k0 << 16);
+        d[pt / 2] = h1 | ((uint32_t)k1 << 16);
+        d[pt] = h2 | ((uint32_t)k2 << 16);
       }
     }
     __syncthreads();
@@ -139,10 +149,10 @@ __global__ void __launch_bounds__(256) k_bslice(BDenseArgs g) {
 
 // ---------------------------------------------------------------- products
 
-// K steps of one output tile: the nonzero K blocks of H_A's row tile
-// (H_A Psi), then those of H_B's row tile (Psi H_B^T); entry = kb, plus 32
-// for the second product.  A tile with none gets one zero block (which
-// clears its accumulators).
+// K steps of one output tile: the nonzero 64-wide K blocks of H_A's row
+// tile (H_A Psi), then those of H_B's row tile (Psi H_B^T); entry = kb, plus
+// 32 for the second product (kb < 16 as d <= 1024).  A tile with none gets
+// one zero block (which clears its accumulators).
 template <int BN>
 __device__ __forceinline__ int tile_steps(const BInst& I, int m0, int n0, unsigned char* ks) {
   const int tmA = (I.dA + kBdBM - 1) / kBdBM, tn64 = (I.dB + 63) / 64;
@@ -363,15 +373,23 @@ __global__ void __launch_bounds__(kBdThreads, 1) k_bgemm(BDenseArgs g, int which
         const float bd = cv ? Bd[col] : 0.f;
         const float* __restrict__ xc = x + (long long)r0 * dB + col;
         float* __restrict__ yc = y + (long long)r0 * dB + col;
-#pragma unroll 4
+        // all 32 rows' x loads in flight before any is used (x is read from
+        // DRAM here: one load at a time per warp would leave the epilogue
+        // bound by memory latency)
+        float xv[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) xv[r] = (r < nr && cv) ? xc[(long long)r * dB] : 0.f;
+#pragma unroll
         for (int r = 0; r < 32; ++r) {
           const uint32_t sa = __shfl_sync(0xffffffffu, sal, r);
           const float da = __shfl_sync(0xffffffffu, dal, r);
           if (r < nr && cv) {
             const uint32_t z = vand ? (sa & sb) : (sa ^ sb);
             float dg = da + bd;
-            for (int q = 0; q < ncls; ++q) dg += w[q] * (float)__popc(z & mk[q]);
-            yc[(long long)r * dB] = fmaf(dg, xc[(long long)r * dB], tr[r * 33 + lane]);
+#pragma unroll
+            for (int q = 0; q < kMaxClasses; ++q)  // unrolled: w, mk stay in registers
+              if (q < ncls) dg += w[q] * (float)__popc(z & mk[q]);
+            yc[(long long)r * dB] = fmaf(dg, xv[r], tr[r * 33 + lane]);
           }
         }
         __syncwarp();
