@@ -330,25 +330,6 @@ size_t tables_bytes(const HostTables& h, bool dense) {
   return b;
 }
 
-// dense side operator (off-diagonal part, from the CSR) as three BF16 pieces
-// [3][d][pad64(d)]
-void side_pieces(const std::vector<int>& rp, const std::vector<int>& col, const std::vector<float>& val, int64_t d,
-                 std::vector<uint16_t>& out) {
-  const int kp = pad64(d);
-  std::vector<float> dense((size_t)d * kp, 0.f);
-  for (int64_t r = 0; r < d; ++r)
-    for (int e = rp[r]; e < rp[r + 1]; ++e) dense[(size_t)r * kp + col[e]] += val[e];
-  out.assign((size_t)3 * d * kp, 0);
-  const size_t plane = (size_t)d * kp;
-  for (size_t i = 0; i < plane; ++i) {
-    uint16_t h[3];
-    bf16_split3_host(dense[i], h);
-    out[i] = h[0];
-    out[plane + i] = h[1];
-    out[2 * plane + i] = h[2];
-  }
-}
-
 // chosen mode per instance shape, shared by every engine of the process
 using ShapeKey = std::array<long long, 4>;
 std::mutex g_mode_mu;
@@ -507,9 +488,10 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
     return ED_ENOMEM;
   }
   // lay the instance out in its arena range: three vectors, the CSR tables
-  // and the H pieces (uploaded together), the Psi pieces (scratch)
+  // (uploaded), the dense form's tables (built on the device) and the Psi
+  // pieces (scratch)
   const size_t tab0 = align256((size_t)3 * h.dA * h.dB * 4);
-  const size_t up_end = tab0 + csr_bytes(h) + (dn ? h_piece_bytes(h) : 0);
+  const size_t up_end = tab0 + csr_bytes(h);
   std::vector<char> host(up_end, 0);
   size_t cur = tab0;
   BSlot& S = slots_[slot];
@@ -553,23 +535,11 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
   S.key[3] = h.B_rp.back();
   d.mode = kModeCSR;
   if (dn) {
-    std::vector<uint16_t> pa, pb;
-    side_pieces(h.A_rp, h.A_col, h.A_val, h.dA, pa);
-    side_pieces(h.B_rp, h.B_col, h.B_val, h.dB, pb);
     d.KpA = pad64(h.dA);
     d.KpB = pad64(h.dB);
-    d.HA = (const uint16_t*)put(pa.data(), pa.size() * 2);
-    d.HB = (const uint16_t*)put(pb.data(), pb.size() * 2);
-    std::vector<uint32_t> km(kmask_words(h), 0u);
-    const size_t tmA = (h.dA + 127) / 128, tn64 = (h.dB + 63) / 64;
-    for (int64_t r = 0; r < h.dA; ++r)
-      for (int e = h.A_rp[r]; e < h.A_rp[r + 1]; ++e) km[r / 128] |= 1u << (h.A_col[e] / 64);
-    for (int64_t r = 0; r < h.dB; ++r)
-      for (int e = h.B_rp[r]; e < h.B_rp[r + 1]; ++e) {
-        km[tmA + r / 64] |= 1u << (h.B_col[e] / 64);
-        km[tmA + tn64 + r / 128] |= 1u << (h.B_col[e] / 64);
-      }
-    d.kmask = (const uint32_t*)put(km.data(), km.size() * 4);
+    d.HA = (const uint16_t*)put(nullptr, (size_t)3 * h.dA * d.KpA * 2);
+    d.HB = (const uint16_t*)put(nullptr, (size_t)3 * h.dB * d.KpB * 2);
+    d.kmask = (const uint32_t*)put(nullptr, kmask_words(h) * 4);
     d.XN = (uint16_t*)put(nullptr, (size_t)3 * h.dA * d.KpB * 2);
     d.XT = (uint16_t*)put(nullptr, (size_t)3 * h.dB * d.KpA * 2);
     // A-role maps (H_A, Psi) with 128-row boxes; B-role maps (Psi^T, H_B)
@@ -584,6 +554,10 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
     ED_CUDA_TRY(cudaMemcpyAsync(d_maps_ + (size_t)slot * kBMaps, mp, sizeof(mp), cudaMemcpyHostToDevice, st_));
   }
   ED_CUDA_TRY(cudaMemcpyAsync(arena_ + off + tab0, host.data() + tab0, up_end - tab0, cudaMemcpyHostToDevice, st_));
+  if (dn) {
+    ED_CUDA_TRY(cudaMemsetAsync(arena_ + off + up_end, 0, h_piece_bytes(h), st_));
+    ED_TRY(bdense_tables(d, st_));
+  }
   S.used = true;
   S.active = false;
   S.alloc_off = off;

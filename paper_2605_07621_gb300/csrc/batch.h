@@ -80,10 +80,9 @@ struct BDenseArgs {
 };
 ed_status bdense_prepare();  // kernel attributes; once, before any graph capture
 ed_status bdense_apply(const BDenseArgs& a, cudaStream_t st);
-// the three BF16 pieces (bit patterns) of an FP32 value: v = h0 + h1 + h2
-// to 24 significant bits (each piece the rounding of what the previous ones
-// leave)
-void bf16_split3_host(float v, uint16_t* h);
+// the dense form's tables of one instance (pieces of H_A, H_B, nonzero-block
+// masks; their arena ranges zeroed first) built on the device from its CSR
+ed_status bdense_tables(const BInst& I, cudaStream_t st);
 
 // host side of one instance
 struct BSlot {

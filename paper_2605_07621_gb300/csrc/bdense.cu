@@ -58,27 +58,6 @@ struct BdCfg {
 
 // ---------------------------------------------------------------- pieces
 
-static uint16_t bf16_rn_host(float f) {  // round to nearest even (finite values)
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  u += 0x7FFFu + ((u >> 16) & 1u);
-  return (uint16_t)(u >> 16);
-}
-static float bf16_value_host(uint16_t h) {
-  const uint32_t u = (uint32_t)h << 16;
-  float f;
-  std::memcpy(&f, &u, 4);
-  return f;
-}
-
-void bf16_split3_host(float v, uint16_t* h) {
-  h[0] = bf16_rn_host(v);
-  const float r1 = v - bf16_value_host(h[0]);
-  h[1] = bf16_rn_host(r1);
-  const float r2 = r1 - bf16_value_host(h[1]);
-  h[2] = bf16_rn_host(r2);
-}
-
 __device__ __forceinline__ void split3_dev(float v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
   const __nv_bfloat16 a = __float2bfloat16_rn(v);
   const float r1 = v - __bfloat162float(a);
@@ -145,6 +124,55 @@ __global__ void __launch_bounds__(256) k_bslice(BDenseArgs g) {
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------- tables
+
+// Dense H_A, H_B pieces and their nonzero-K-block masks from the instance's
+// CSR rows (zeroed beforehand): one thread per row of either side; entries
+// with the same column are summed before the split.
+__global__ void k_btables(BInst I) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool onA = r < I.dA;
+  if (r >= (long long)I.dA + I.dB) return;
+  const long long row = onA ? r : r - I.dA;
+  const int d = onA ? I.dA : I.dB;
+  const int* rp = onA ? I.A_rp : I.B_rp;
+  const int* col = onA ? I.A_col : I.B_col;
+  const float* val = onA ? I.A_val : I.B_val;
+  uint16_t* P = const_cast<uint16_t*>(onA ? I.HA : I.HB);
+  const int kp = onA ? I.KpA : I.KpB;
+  const long long plane = (long long)d * kp;
+  uint32_t* km = const_cast<uint32_t*>(I.kmask);
+  const int tmA = (I.dA + kBdBM - 1) / kBdBM, tn64 = (I.dB + 63) / 64;
+  for (int e = rp[row]; e < rp[row + 1]; ++e) {
+    const int c = col[e];
+    bool seen = false;
+    for (int f = rp[row]; f < e; ++f) seen = seen || col[f] == c;
+    if (seen) continue;
+    float v = 0.f;
+    for (int f = e; f < rp[row + 1]; ++f)
+      if (col[f] == c) v += val[f];
+    uint16_t h0, h1, h2;
+    split3_dev(v, h0, h1, h2);
+    P[row * kp + c] = h0;
+    P[plane + row * kp + c] = h1;
+    P[2 * plane + row * kp + c] = h2;
+    const uint32_t bit = 1u << (c / kBdBK);
+    if (onA) {
+      atomicOr(&km[row / kBdBM], bit);
+    } else {
+      atomicOr(&km[tmA + row / 64], bit);
+      atomicOr(&km[tmA + tn64 + row / 128], bit);
+    }
+  }
+}
+
+ed_status bdense_tables(const BInst& I, cudaStream_t st) {
+  const long long n = (long long)I.dA + I.dB;
+  k_btables<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(I);
+  ED_CUDA_TRY(cudaGetLastError());
+  return ED_OK;
 }
 
 // ---------------------------------------------------------------- products
