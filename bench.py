@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--pipes", action="store_true", help="build and run the pipe-rate microbenchmark, then exit")
     p.add_argument("--dense-only", action="store_true",
                    help="run only the dense-block (digit-split tensor-core) measurement and print it")
+    p.add_argument("--batched-only", action="store_true",
+                   help="run only the batched measurement (no serving sweep) and print it")
     p.add_argument("--no-configs", action="store_true", help="skip the Heis16 / Hub12 / Hub4x4 measurements")
     p.add_argument("--no-entangle", action="store_true", help="skip the entanglement spectrum of the ground state")
     p.add_argument("--no-dense", action="store_true", help="skip the dense-block (DMRG-style) H psi")
@@ -336,7 +338,8 @@ def cpu_baseline(model, budget_s: float = 12.0):
             "rows_per_s": rows_per_s, "index_build_s": smp.t_index, "value_with_index_build": with_index}
 
 
-def batched_and_served(ed, n: int, rate: float, seed: int = 20260507, rank: int = 0, world: int = 1):
+def batched_and_served(ed, n: int, rate: float, seed: int = 20260507, rank: int = 0, world: int = 1,
+                       serve: bool = True):
     """512 independent Hubbard instances (this rank's share when several GPUs
     run): one batched Lanczos solve, then the same instances as a Poisson
     stream of requests to the serving loop."""
@@ -390,6 +393,8 @@ def batched_and_served(ed, n: int, rate: float, seed: int = 20260507, rank: int 
                "hpsi_per_s_aggregate": float(np.sum(it)) / t_solve, "steps": info["steps"],
                "all_converged": info["all_converged"], "storage": "f32", "reductions": "f64"}
     del x, y, b
+    if not serve:
+        return batched, None
     # served: Poisson arrivals, continuous batching, arrival rate swept up to
     # `rate` (the last, highest rate is the headline entry)
     sweep = []
@@ -526,6 +531,11 @@ def main():
         import paper_2605_07621_gb300 as ed
 
         print(json.dumps(dense_blocks_section(ed)), flush=True)
+        return
+    if args.batched_only:
+        import paper_2605_07621_gb300 as ed
+
+        print(json.dumps(batched_and_served(ed, args.batch_n, args.serve_rate, serve=False)[0]), flush=True)
         return
     ws, rank, local = dist_env()
     if ws > 1:
