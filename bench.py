@@ -440,14 +440,15 @@ def other_configs(ed):
         return r, time.perf_counter() - t0
 
     # the headline lattice with a coupling that is not a dyadic rational
-    # (J2 = 0.3): fixed-point sums per value class, weighted in FP64
+    # (J2 = 0.3): fixed-point class sums with 64-bit integer weights, exact 128-bit sums
     ctx = ed.build_local_ops(ed.build_sectors(W.j1j2_torus(8, 4, 1.0, 0.3, 16, 0xFFFF)))
     x = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
     ed.random_vector(ctx, x)
     y = torch.empty_like(x)
     ed.apply_H(ctx, x, y)
     _, t1 = timed(lambda: [ed.apply_H(ctx, x, y) for _ in range(5)])
-    out["j1j2_4x8_j2_0.3"] = {"states": ctx.dim, "hpsi_per_s_f64": 5 / t1, "ms_per_hpsi": 1e3 * t1 / 5}
+    out["j1j2_4x8_j2_0.3"] = {"states": ctx.dim, "hpsi_per_s_f64": 5 / t1, "ms_per_hpsi": 1e3 * t1 / 5,
+                              "fp64_mode": ctx.fp64_mode()}
     del x, y, ctx
     torch.cuda.empty_cache()
     ctx = ed.build_local_ops(ed.build_sectors(W.config_heis16()))

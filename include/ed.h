@@ -365,6 +365,15 @@ ed_status ed_profile_read(ed_ctx* ctx, double* ms, int64_t* count, int reset);
  * plain per-row kernel (the class-sorted kernels do not apply), 1 = the
  * class-sorted row pass (k_row5); negative: ed_build_local_ops has not run. */
 int ed_row_pass(const ed_ctx* ctx, ed_dtype dtype);
+/* Arithmetic of the FP64 apply on this context (Eq. (2) evaluated on a
+ * fixed-point copy of x unless 0): 0 = FP64 arithmetic per matrix element;
+ * 1 = every coupling dyadic: exact 64-bit integer sums, rounded once;
+ * 2 = couplings not dyadic: class sums weighted by 64-bit integers (every
+ *     FP64 coupling and diagonal term as an integer multiple of one power of
+ *     two) into exact 128-bit sums, rounded once per pass;
+ * 3 = value range too wide for 2: class sums weighted in FP64.
+ * Negative: ed_build_local_ops has not run. */
+int ed_fp64_mode(const ed_ctx* ctx);
 
 /* ---- queries ---------------------------------------------------------- */
 int64_t ed_dim(const ed_ctx* ctx);

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("ed_profile_enable", c_int, [c_void_p, c_int]),
     ("ed_profile_read", c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     ("ed_row_pass", c_int, [c_void_p, c_int]),
+    ("ed_fp64_mode", c_int, [c_void_p]),
     ("ed_dim", c_int64, [c_void_p]),
     ("ed_num_blocks", c_int, [c_void_p]),
     ("ed_blocks", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

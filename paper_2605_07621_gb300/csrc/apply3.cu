@@ -1,12 +1,18 @@
-// Class-sorted H|psi> (paper Eq. (2)) in three arithmetic flavours:
+// Class-sorted H|psi> (paper Eq. (2)) in these arithmetic flavours:
 //   FP32  storage and accumulation;
-//   FP64  storage and accumulation (models with non-dyadic couplings);
+//   FP64  storage and accumulation (fallback);
 //   I64   FP64 storage, exact 64-bit fixed-point accumulation: when every
-//         matrix element is an integer multiple of 2^-q_shift, x is scaled
-//         by one power of two per vector, summed exactly on the integer
-//         pipe and rounded once back to FP64.  FP64 adds and FP64
+//         matrix element is a small integer multiple of 2^-q_shift, x is
+//         scaled by one power of two per vector, summed exactly on the
+//         integer pipe and rounded once back to FP64.  FP64 adds and FP64
 //         conversions run at about 0.5 T/s on this GPU, the integer pipe at
-//         tens of T/s, so no FP64 instruction is issued per matrix element.
+//         tens of T/s, so no FP64 instruction is issued per matrix element;
+//   W128  the same for couplings that are not dyadic: FP64 values are
+//         integer multiples of 2^-q_shift with up to 53-bit integers, so the
+//         class sums are weighted by 64-bit integers into exact 128-bit sums,
+//         rounded to FP64 once per pass;
+//   C64   fixed-point class sums weighted in FP64 (value ranges too wide
+//         for 64-bit integer weights).
 // Row pass (k_row5): the diagonal, the H_B (column-mixing) term and the
 // cross-cut terms of whole rows.  psi_s[a,:] is staged in shared memory by
 // bulk TMA copies, then each column b sums, class by class, its H_B
@@ -24,6 +30,17 @@ namespace edk {
 // host entry points of the two conversions (used by the CPU tests)
 long long host_to_fixed(double v, int sh_base) { return to_fixed(v, sh_base); }
 double host_from_fixed(long long Y, int e2) { return from_fixed(Y, e2); }
+double host_from_fixed128(long long hi, unsigned long long lo, int e2) {
+  I128 v;
+  v.hi = hi;
+  v.lo = lo;
+  return from_fixed128(v, e2);
+}
+void host_mul_wide(long long a, long long b, long long* hi, unsigned long long* lo) {
+  const I128 v = mul_wide(a, b);
+  *hi = v.hi;
+  *lo = v.lo;
+}
 
 // largest biased exponent of x (atomic max into out[0]; out must start at 0)
 __global__ void k_exp_max(const double* __restrict__ x, long long n, int* out) {
@@ -209,7 +226,7 @@ __global__ void __launch_bounds__(NT, MINB)
       const uint2 m = t.B_meta4[gB];
       const unsigned pb = t.B_pack[gB];
       const typename Pol::D dbv = Pol::diagB(t, gB);
-      typename Pol::Y acc[R];
+      typename Pol::A acc[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const unsigned z = t.vab_and ? (pa[r] & pb) : (pa[r] ^ pb);
@@ -406,11 +423,11 @@ __global__ void __launch_bounds__(256) k_panel4(P3 p, const int4* __restrict__ i
       const bool full = it.y + sp + W <= dB;
       const S* xb0 = xb + b0;                                              // column b0 of row 0
       const S* zr = reinterpret_cast<const S*>(g_zero_row) + lane;         // zeros at +32c
-      typename Pol::Y acc[NC];
+      typename Pol::A acc[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const long long b = b0 + 32 * c;
-        acc[c] = b < dB ? yrow[b] : (typename Pol::Y)0;
+        acc[c] = typename Pol::A(b < dB ? yrow[b] : (typename Pol::Y)0);
       }
       unsigned e = m.x;
 #pragma unroll
@@ -613,11 +630,12 @@ static ed_status apply_fixed(ed_ctx* c, const double* x, double* y, long long* f
     ED_TRY(run_v3<PI64>(c, fixed, (long long*)y, emax, st, pm));
     return diag_add(c, x, y, st);
   }
-  return run_v3<PC64>(c, fixed, y, emax, st, pm);
+  return c->wide ? run_v3<PW>(c, fixed, y, emax, st, pm) : run_v3<PC64>(c, fixed, y, emax, st, pm);
 }
 
-// fixed-point input: exact integer sums, either with integer weights (dyadic
-// couplings) or with FP64 weights per value class
+// fixed-point input: exact integer sums, with small integer weights (dyadic
+// couplings), with 64-bit integer weights into 128-bit sums (other couplings)
+// or, when their range is too wide for that, with FP64 weights per value class
 static bool fixed_mode(const ed_ctx* c) { return c->dyadic || c->classed; }
 
 bool fixed_path(const ed_ctx* c, const void* x) { return fixed_mode(c) && v3_usable(c, ED_F64, x); }
@@ -636,7 +654,7 @@ ed_status apply_prepared_fixed(ed_ctx* c, const double* x, double* y, cudaStream
     r = run_v3<PI64>(c, c->d_fixed, (long long*)y, c->d_exp, st, pm);
     if (r == ED_OK) r = diag_add(c, x, y, st);
   } else {
-    r = run_v3<PC64>(c, c->d_fixed, y, c->d_exp, st, pm);
+    r = c->wide ? run_v3<PW>(c, c->d_fixed, y, c->d_exp, st, pm) : run_v3<PC64>(c, c->d_fixed, y, c->d_exp, st, pm);
   }
   pm.mark(4, st);
   pm.end(c);
@@ -735,6 +753,13 @@ extern "C" int ed_row_pass(const ed_ctx* c, ed_dtype dt) {
   if (!c || !c->ops_built) return -1;
   if (!v3_usable(c, dt, (const void*)(uintptr_t)256)) return 0;  // any 16-byte aligned x
   return 1;
+}
+
+extern "C" int ed_fp64_mode(const ed_ctx* c) {
+  if (!c || !c->ops_built) return -1;
+  if (c->dyadic) return 1;
+  if (c->classed) return c->wide ? 2 : 3;
+  return 0;
 }
 
 extern "C" ed_status ed_profile_enable(ed_ctx* c, int enable) {

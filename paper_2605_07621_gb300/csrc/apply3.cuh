@@ -23,11 +23,12 @@ struct P3 {
 };
 
 // Policy types: S = staged / gathered values (and per-class sums), Y = the
-// accumulator and the partial output kept in y between the passes, D = the
+// partial output kept in y between the passes, A = the accumulator, D = the
 // diagonal, W = the per-class weights; dmul / wmul combine them.
 struct PF32 {
   using S = float;
   using Y = float;
+  using A = float;
   using D = float;
   using W = float;
   __device__ static float dmul(float d, float x) { return d * x; }
@@ -50,6 +51,7 @@ struct PF32 {
 struct PF64 {
   using S = double;
   using Y = double;
+  using A = double;
   using D = double;
   using W = double;
   __device__ static double dmul(double d, double x) { return d * x; }
@@ -72,6 +74,7 @@ struct PF64 {
 struct PI64 {
   using S = long long;
   using Y = long long;
+  using A = long long;
   using D = long long;
   using W = long long;
   __device__ static long long dmul(long long d, long long x) { return d * x; }
@@ -101,6 +104,7 @@ struct PI64 {
 struct PC64 {
   using S = long long;
   using Y = double;
+  using A = double;
   using D = double;
   using W = double;
   __device__ static double dmul(double d, long long x) { return d * (double)x; }
@@ -110,6 +114,61 @@ struct PC64 {
   __device__ static double diagA(const Dev3& t, long long gA) { return t.A_d64[gA] + t.dc0_64; }
   __device__ static double diagB(const Dev3& t, long long gB) { return t.B_d64[gB]; }
   __device__ static double vab(const Dev3& t, unsigned z) { return PF64::vab(t, z); }
+};
+
+// 128-bit two's-complement integer: sums of products of 64-bit integers
+struct I128 {
+  unsigned long long lo;
+  long long hi;
+};
+__host__ __device__ __forceinline__ I128 operator+(I128 a, I128 b) {
+  I128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1 : 0);
+  return r;
+}
+__host__ __device__ __forceinline__ I128 mul_wide(long long a, long long b) {
+  I128 r;
+  r.lo = (unsigned long long)a * (unsigned long long)b;
+#ifdef __CUDA_ARCH__
+  r.hi = __mul64hi(a, b);
+#else
+  r.hi = (long long)(((__int128)a * (__int128)b) >> 64);
+#endif
+  return r;
+}
+
+// Wide integer weights (models whose couplings are not dyadic): every
+// coupling and diagonal value is an FP64 number, i.e. an integer multiple of
+// 2^-q_shift for one q_shift that covers them all; the class sums of the
+// fixed-point x are multiplied by these 64-bit integer weights into an exact
+// 128-bit sum, rounded once to FP64 per pass by bit manipulation (no FP64
+// instruction per matrix element).  The row pass's partial result is kept in
+// y as FP64 and the panel pass adds its own rounded sum to it.
+struct AccW {
+  I128 s;    // exact sum of this pass
+  double p;  // partial result of the row pass (panel pass only)
+  __device__ AccW() {}
+  __device__ AccW(I128 v) : s(v), p(0.0) {}
+  __device__ AccW(double v) : p(v) { s.lo = 0ull; s.hi = 0ll; }
+  __device__ AccW& operator+=(I128 v) {
+    s = s + v;
+    return *this;
+  }
+};
+struct PW {
+  using S = long long;
+  using Y = double;
+  using A = AccW;
+  using D = long long;
+  using W = long long;
+  __device__ static I128 dmul(long long d, long long x) { return mul_wide(d, x); }
+  __device__ static I128 wmul(long long w, long long s) { return mul_wide(w, s); }
+  __device__ static long long w(const Dev3& t, int c) { return t.wI[c]; }
+  __device__ static long long bw(const Dev3& t, int k) { return t.bond_wI[k]; }
+  __device__ static long long diagA(const Dev3& t, long long gA) { return t.A_dW[gA] + t.dc0_I; }
+  __device__ static long long diagB(const Dev3& t, long long gB) { return t.B_dW[gB]; }
+  __device__ static long long vab(const Dev3& t, unsigned z) { return PI64::vab(t, z); }
 };
 
 // ---------------------------------------------------------------- fixed point <-> FP64 by bit manipulation
@@ -188,10 +247,49 @@ __host__ __device__ __forceinline__ double from_fixed(long long Y, int e2) {
   return bits_f64((s << 63) | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull));
 }
 
+// v * 2^e2 rounded to nearest (ties to even) FP64, v a 128-bit integer
+__host__ __device__ __forceinline__ double from_fixed128(I128 v, int e2) {
+  const unsigned long long s = v.hi < 0 ? 1ull : 0ull;
+  unsigned long long lo = v.lo, hi = (unsigned long long)v.hi;
+  if (s) {  // magnitude
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  if (hi == 0ull && lo == 0ull) return 0.0;
+  // normalise: leading one at bit 63 of h, the bits below it in h then l
+  int p;
+  unsigned long long h, l;
+  if (hi != 0ull) {
+    const int n = clz64(hi);
+    p = 127 - n;
+    h = n == 0 ? hi : (hi << n) | (lo >> (64 - n));
+    l = lo << n;
+  } else {
+    const int n = clz64(lo);
+    p = 63 - n;
+    h = lo << n;
+    l = 0ull;
+  }
+  unsigned long long mant = h >> 11;  // 53 bits
+  const unsigned long long rbit = (h >> 10) & 1ull;
+  const bool sticky = (h & 0x3FFull) != 0ull || l != 0ull;
+  if (rbit && (sticky || (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++p;
+    }
+  }
+  const int ex = p + e2 + 1023;
+  if (ex <= 0) return s ? -0.0 : 0.0;
+  if (ex >= 2047) return bits_f64((s << 63) | (0x7ffull << 52));
+  return bits_f64((s << 63) | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull));
+}
+
 __device__ __forceinline__ int out_exp(const Dev3& t, const int* emax) { return (emax[0] - 1022) - t.P - t.q_shift; }
 
 template <class Pol>
-__device__ __forceinline__ void store_out(typename Pol::Y* y, long long i, typename Pol::Y v, bool final_,
+__device__ __forceinline__ void store_out(typename Pol::Y* y, long long i, typename Pol::A v, bool final_,
                                           int e2) {
   y[i] = v;
 }
@@ -203,6 +301,10 @@ __device__ __forceinline__ void store_out<PI64>(long long* y, long long i, long 
 template <>
 __device__ __forceinline__ void store_out<PC64>(double* y, long long i, double v, bool final_, int e2) {
   y[i] = final_ ? ldexp(v, e2) : v;
+}
+template <>
+__device__ __forceinline__ void store_out<PW>(double* y, long long i, AccW v, bool final_, int e2) {
+  y[i] = v.p + from_fixed128(v.s, e2);  // both passes store real values
 }
 
 // ---------------------------------------------------------------- TMA / mbarrier

@@ -171,6 +171,8 @@ struct Dev3 {
   const double* B_d64;
   const int* A_dI;          // side diagonal in units of 2^-q_shift
   const int* B_dI;
+  const long long* A_dW;    // the same as 64-bit integers (wide-weight path)
+  const long long* B_dW;
   const uint16_t* mapA;     // [n_cross_A_bits][A_total]
   const uint16_t* mapB;     // [n_cross_B_bits][B_total]
   long long A_total, B_total;
@@ -265,6 +267,7 @@ struct ed_ctx {
   // class-sorted path
   bool v3_ok = false;                // tables below are valid
   bool dyadic = false;               // FP64 apply may use exact fixed point
+  bool wide = false;                 // couplings not dyadic: integer weights, exact 128-bit sums
   bool classed = false;              // couplings not dyadic: the FP64 apply sums the fixed-point
                                      // input exactly per value class and weights each sum in FP64
   bool diag_split = false;           // ... for the off-diagonal terms only; the

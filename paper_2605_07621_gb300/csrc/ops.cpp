@@ -293,8 +293,13 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   if (!c->dyadic) c->diag_split = false;
   // couplings that are not dyadic: fixed-point input summed exactly per value
   // class (at most the largest per-class count of one row's terms in one
-  // pass, plus the cross bonds), each class sum weighted in FP64
+  // pass, plus the cross bonds).  Every FP64 coupling and diagonal value is
+  // an integer multiple of 2^-qw, qw from the smallest unit among them; when
+  // those integers fit 61 bits they are the 64-bit weights of exact 128-bit
+  // sums (wide path), otherwise each class sum is weighted in FP64
   c->classed = false;
+  c->wide = false;
+  std::vector<long long> AdW, BdW;
   if (!c->dyadic) {
     long long mx = 1;
     for (const Side3* s3 : {&a3, &b3})
@@ -305,6 +310,82 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
     t.q_shift = 0;
     t.P = std::min(60, 62 - bits);
     c->classed = t.P >= 40;
+    // the values the wide path multiplies: off-diagonal classes, cross-bond
+    // coefficients, and the terms of the diagonal (bond jz / 4, on-site
+    // energies, the cross-cut diagonal's weights); the side diagonals and
+    // c0 are then exact integer sums of these terms (not the rounded FP64
+    // sums, whose cancellation residues would need far smaller units)
+    const bool hub = c->kind == ED_HUBBARD;
+    std::vector<double> base(cls.begin(), cls.end());
+    for (const auto& cr : c->cross) {
+      base.push_back(cr.coef);
+      base.push_back(0.25 * cr.jz);
+    }
+    for (int q = 0; q < dp.ncls; ++q) base.push_back(dp.w[q]);
+    for (const auto* bl : {&c->bondsA, &c->bondsB})
+      for (const auto& b : *bl) base.push_back(0.25 * b.jz);
+    if (hub)
+      for (double e : c->eps) base.push_back(e);
+    int emin = 1 << 30, emx = -(1 << 30);
+    for (double v : base)
+      if (v != 0.0 && std::isfinite(v)) {
+        const int e = std::ilogb(v);
+        emin = std::min(emin, e - 52);
+        emx = std::max(emx, e);
+      }
+    if (c->classed && emin < (1 << 30) && emx - emin <= 55) {
+      const int qw = -emin;
+      auto W = [&](double v) { return (long long)std::ldexp(v, qw); };  // exact: v is k 2^-qw, |k| < 2^56
+      long long wW[kMaxCls] = {0, 0, 0, 0}, dwW[kMaxClasses] = {};
+      for (size_t i = 0; i < cls.size(); ++i) wW[i] = W(cls[i]);
+      for (int q = 0; q < dp.ncls; ++q) dwW[q] = W(dp.w[q]);
+      long long c0W = 0;
+      if (!hub)
+        for (const auto& cr : c->cross) c0W += W(0.25 * cr.jz);
+      auto side_diag = [&](const Side& sd, const std::vector<ed_ctx::SideBond>& bonds, std::vector<long long>& out) {
+        out.assign(sd.total(), 0);
+        for (int64_t g = 0; g < sd.total(); ++g) {
+          const uint32_t x = sd.states[g];
+          long long d = 0;
+          if (!hub) {
+            for (const auto& b : bonds) d += (((x >> b.p) & 1) == ((x >> b.q) & 1) ? 1 : -1) * W(0.25 * b.jz);
+          } else {
+            for (int p = 0; p < sd.n; ++p)
+              if ((x >> p) & 1) d += W(c->eps[sd.sites[p]]);
+          }
+          out[g] = d;
+        }
+      };
+      side_diag(c->A, c->bondsA, AdW);
+      side_diag(c->B, c->bondsB, BdW);
+      // the integer diagonal fits 62 bits, the 128-bit sums fit with P bits of x
+      double dmax = std::fabs((double)c0W);
+      for (int q = 0; q < dp.ncls; ++q) dmax += std::fabs((double)dwW[q]) * __builtin_popcountll(dp.mask[q]);
+      auto side_max = [&](const Side3& s3, const std::vector<long long>& dW, double* dm) {
+        double m = 0.0, d = 0.0;
+        for (size_t g = 0; g < s3.meta.size(); ++g) {
+          double r = std::fabs((double)dW[g]);
+          d = std::max(d, r);
+          for (int cc = 0; cc < kMaxCls; ++cc) r += ((s3.meta[g].y >> (8 * cc)) & 255u) * std::fabs((double)wW[cc]);
+          m = std::max(m, r);
+        }
+        *dm += d;
+        return m;
+      };
+      double rmax = side_max(a3, AdW, &dmax) + side_max(b3, BdW, &dmax) + std::fabs((double)c0W);
+      for (int q = 0; q < dp.ncls; ++q) rmax += std::fabs((double)dwW[q]) * __builtin_popcountll(dp.mask[q]);
+      for (size_t k = 0; k < c->cross.size(); ++k) rmax += std::fabs((double)wW[c->cross_cls[k]]);
+      const int Pw = std::min(t.P, 126 - (int)std::ceil(std::log2(rmax + 1.0)));
+      if (dmax < 4.6e18 && Pw >= 40) {
+        c->wide = true;
+        t.P = Pw;
+        t.q_shift = qw;
+        for (int i = 0; i < kMaxCls; ++i) t.wI[i] = wW[i];
+        for (size_t k = 0; k < c->cross.size(); ++k) t.bond_wI[k] = W(c->cross[k].coef);
+        for (int q = 0; q < dp.ncls; ++q) t.dwI[q] = dwW[q];
+        t.dc0_I = c0W;
+      }
+    }
   }
   // upload
   uint2 *Am, *Bm;
@@ -317,9 +398,14 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   ED_TRY(upload(c, &Bc, b3.col));
   ED_TRY(upload(c, &Ap, a3.pack));
   ED_TRY(upload(c, &Bp, b3.pack));
+  long long *AdWd = nullptr, *BdWd = nullptr;
   if (c->dyadic) {
     ED_TRY(upload(c, &AdI, a3.dI));
     ED_TRY(upload(c, &BdI, b3.dI));
+  }
+  if (c->wide) {
+    ED_TRY(upload(c, &AdWd, AdW));
+    ED_TRY(upload(c, &BdWd, BdW));
   }
   std::vector<uint16_t> ma(ha.maps.size()), mb(hb.maps.size());
   for (size_t i = 0; i < ma.size(); ++i) ma[i] = ha.maps[i] < 0 ? 0xFFFF : (uint16_t)ha.maps[i];
@@ -336,7 +422,7 @@ static ed_status build_v3(ed_ctx* c, const HostSideOps& ha, const HostSideOps& h
   t.B_meta4 = Bm4;
   t.B_col4 = Bc4;
   t.A_meta = Am; t.B_meta = Bm; t.A_col = Ac; t.B_col = Bc; t.A_pack = Ap; t.B_pack = Bp;
-  t.A_dI = AdI; t.B_dI = BdI; t.mapA = mA; t.mapB = mB;
+  t.A_dI = AdI; t.B_dI = BdI; t.A_dW = AdWd; t.B_dW = BdWd; t.mapA = mA; t.mapB = mB;
   t.A_d32 = c->tab.A_diag32; t.B_d32 = c->tab.B_diag32; t.A_d64 = c->tab.A_diag; t.B_d64 = c->tab.B_diag;
   t.A_total = c->A.total();
   t.B_total = c->B.total();

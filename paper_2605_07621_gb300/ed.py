@@ -102,6 +102,15 @@ class Context:
         """Per-stage CUDA-event timing of apply_H (see ed_profile_enable)."""
         L.check(L.load().ed_profile_enable(self._h, 1 if enable else 0))
 
+    def fp64_mode(self) -> str:
+        """Arithmetic of the FP64 apply (see ed_fp64_mode): "fp64", "fixed"
+        (dyadic couplings), "wide" (128-bit integer weights) or "classed"
+        (FP64 weights per value class)."""
+        k = int(L.load().ed_fp64_mode(self._h))
+        if k < 0:
+            raise RuntimeError("build_local_ops has not run on this context")
+        return ("fp64", "fixed", "wide", "classed")[k]
+
     def row_pass(self, dtype) -> str:
         """Row-pass kernel apply_H runs for ``dtype`` (see ed_row_pass)."""
         import torch

@@ -68,3 +68,64 @@ def test_roundtrip_relative_error(conv):
     P, E = 52, 0
     back = np.array([fr_f(to_f(v, P - E), E - P) for v in x])
     assert np.max(np.abs(back - x)) <= 2.0 ** (E - P - 1)
+
+
+@pytest.fixture(scope="module")
+def wide():
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("_ed_build", os.path.join(ROOT, "paper_2605_07621_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(mod.build())
+    fr = getattr(lib, "_ZN3edk18host_from_fixed128Exyi")
+    fr.restype = ctypes.c_double
+    fr.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.c_int]
+    mw = getattr(lib, "_ZN3edk13host_mul_wideExxPxPy")
+    mw.restype = None
+    mw.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
+                   ctypes.POINTER(ctypes.c_ulonglong)]
+    return fr, mw
+
+
+def _split128(v: int):
+    u = v & ((1 << 128) - 1)
+    hi = u >> 64
+    if hi >= 1 << 63:
+        hi -= 1 << 64
+    return hi, u & ((1 << 64) - 1)
+
+
+def test_mul_wide_exact(wide):
+    """64 x 64 -> 128-bit signed products of the wide-weight path, against
+    Python integers (two's complement halves)."""
+    _, mw = wide
+    rng = random.Random(3)
+    cases = [(0, 0), (1, -1), (-(1 << 63), -(1 << 63)), ((1 << 63) - 1, (1 << 63) - 1), (-(1 << 63), 1),
+             (-1, -1), (123456789, -987654321)]
+    cases += [(rng.randint(-(1 << 63), (1 << 63) - 1), rng.randint(-(1 << 63), (1 << 63) - 1)) for _ in range(5000)]
+    hi, lo = ctypes.c_longlong(), ctypes.c_ulonglong()
+    for a, b in cases:
+        mw(a, b, ctypes.byref(hi), ctypes.byref(lo))
+        assert (hi.value, lo.value) == _split128(a * b), (a, b)
+
+
+def test_from_fixed128_round_to_nearest_even(wide):
+    """128-bit integer * 2^e2 -> FP64, correctly rounded (ties to even),
+    including values whose leading bit is in either half and halfway cases."""
+    fr, _ = wide
+    rng = random.Random(11)
+    cases = [0, 1, -1, (1 << 53) - 1, 1 << 53, (1 << 53) + 1, (1 << 64) - 1, 1 << 64, (1 << 64) + 1,
+             (1 << 117) + (1 << 64), (1 << 117) + (1 << 64) + 1, (1 << 118) + (3 << 65), -(1 << 126),
+             (1 << 126) - 1, -((1 << 126) - 1), (1 << 63), -(1 << 63)]
+    for k in (64, 70, 100, 126):  # exact halfway points at several positions
+        m = (1 << 52) + rng.randrange(1 << 52)
+        sh = k - 52
+        cases += [(m << sh) + (1 << (sh - 1)), ((m | 1) << sh) + (1 << (sh - 1)), -((m << sh) + (1 << (sh - 1)))]
+    cases += [rng.randint(-(1 << 126), 1 << 126) for _ in range(5000)]
+    cases += [rng.randint(-(1 << 70), 1 << 70) for _ in range(2000)]
+    for v in cases:
+        hi, lo = _split128(v)
+        for e2 in (-170, -120, -60, 0, 5):
+            want = float(Fraction(v) * Fraction(2) ** e2)
+            assert fr(hi, lo, e2) == want, (v, e2)

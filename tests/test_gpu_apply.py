@@ -45,6 +45,10 @@ def _models():
         "hub12_particle": W.hubbard_chain(12, 1.0, 4.0, 7, 6),
         "hub12_hole": W.hubbard_chain(12, 1.0, 4.0, 5, 6),
         "hub_rect_dyadic": W.hubbard_torus(2, 4, 1.0, 2.0, 3, 5),
+        # couplings that are not dyadic: 128-bit integer weights (J2 = 0.3),
+        # and a value range too wide for them (J2 = 3e-19: FP64 class weights)
+        "j1j2_4x4_j2_03": W.j1j2_torus(4, 4, 1.0, 0.3, cut_mask=0xFF),
+        "j1j2_4x4_wide_range": W.j1j2_torus(4, 4, 1.0, 3e-19, cut_mask=0xFF),
         "hub_site_U": W.Model("hubbard", 5, W.chain_bonds(5, True), t=1.0, U=[1.0, 2.0, 3.0, 1.0, 0.0],
                               eps=[0.1, -0.2, 0.3, 0.0, 0.5], n_up=2, n_dw=3, spin_cut=True),
         # Anderson impurity (star): one dyadic hybridisation value and disordered
@@ -279,3 +283,13 @@ def test_j1j2_4x7_full_parity(ed, oracle_mod):
             del x, y
         del x64, ctx
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("name,mode", [("j1j2_4x4", "fixed"), ("j1j2_4x4_j2_03", "wide"),
+                                       ("j1j2_4x4_wide_range", "classed"), ("hub_rect_dyadic", "fixed")])
+def test_fp64_mode_selection(ed, name, mode):
+    """Dyadic couplings take the exact 64-bit path, other couplings the
+    128-bit integer weights, a value range beyond 2^55 the FP64 class
+    weights; each of these contexts is also in the FP64 parity list."""
+    ctx = ed.build_local_ops(ed.build_sectors(MODELS[name]))
+    assert ctx.fp64_mode() == mode
