@@ -96,6 +96,28 @@ def test_batch_apply_parity_largest(ed, oracle_mod, flags):
         assert set(modes.tolist()) == {1, 2}
 
 
+def test_batch_apply_mixed_modes(ed, oracle_mod):
+    """One batch whose instances take different forms under ED_OPS_FORCE_DENSE:
+    a 14-site ring with d_A = d_B = 3003 (above the dense limit of 1024: CSR,
+    rows wider than the staged row buffer)
+    between instances that take 64- and 128-wide dense tiles; every output
+    against the oracle, and the user-vector apply twice in a row gives the
+    same bits."""
+    import torch
+
+    big = W.hubbard_chain(14, 1.0, 3.0, 6, 6, pbc=True, tp=0.2)
+    ms = [_largest(1)[0], big] + [m for m in _instances(40) if min(m.n_up, m.n_dw) == 1][:2]
+    modes = _apply_vs_oracle(ed, oracle_mod, ms, 2)
+    assert modes[1] == 0 and modes[0] == 2 and set(modes[2:].tolist()) == {1}
+    b = ed.batch_create(ms, flags=2)
+    x = torch.randn(b.dim, dtype=torch.float32, device="cuda")
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    ed.batch_apply(b, x, y1)
+    ed.batch_apply(b, x, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+
+
 @pytest.mark.parametrize("flags", [0, 1, 2])
 def test_batch_lanczos_vs_oracle(ed, oracle_mod, flags):
     ms = _instances(16, max_dim=8000)
