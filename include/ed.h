@@ -50,7 +50,7 @@ typedef enum {
   ED_ECUDA = 3,        /* a CUDA runtime call failed */
   ED_ENOCONV = 4,      /* Lanczos stopped at max_iter without meeting tol */
   ED_ETIMEOUT = 5,     /* a bounded wait ran out */
-  ED_EUNSUPPORTED = 6, /* valid request outside what this build supports */
+  ED_EUNSUPPORTED = 6, /* valid request outside what the library supports */
   ED_ECANCELLED = 7    /* a served request was cancelled */
 } ed_status;
 
