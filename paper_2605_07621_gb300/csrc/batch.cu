@@ -464,7 +464,7 @@ ed_status BatchEngine::instance_bytes(const ed_model_desc& m, bool dense, size_t
   return ED_OK;
 }
 
-ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out) {
+ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out, bool commit) {
   // the calling thread may be new to CUDA (the serving worker): make the
   // device's context current for the tensor-map encoding (a driver call)
   ED_DEVICE_SCOPE(device_);
@@ -564,14 +564,15 @@ ed_status BatchEngine::add(const ed_model_desc& m, uint64_t seed, int* slot_out)
   S.alloc_len = need;
   S.dense_ok = dn ? 1 : 0;
   d.mode = dn ? default_mode(S) : kModeCSR;
+  // (copies from pageable host memory return once the source has been staged,
+  // so the host buffers may go; the stream orders everything after them)
   ED_CUDA_TRY(cudaMemcpyAsync(d_inst_ + slot, &d, sizeof(BInst), cudaMemcpyHostToDevice, st_));
-  ED_CUDA_TRY(cudaStreamSynchronize(st_));
-  ED_TRY(restart(slot, seed));
+  ED_TRY(restart(slot, seed, commit));
   *slot_out = slot;
   return ED_OK;
 }
 
-ed_status BatchEngine::restart(int slot, uint64_t seed) {
+ed_status BatchEngine::restart(int slot, uint64_t seed, bool commit) {
   BSlot& S = slots_[slot];
   float* arena_f = (float*)arena_;
   const long long n = S.d.D;
@@ -583,21 +584,21 @@ ed_status BatchEngine::restart(int slot, uint64_t seed) {
   ED_CUDA_TRY(cudaMemsetAsync(d_it_ + slot, 0, sizeof(int), st_));
   ED_CUDA_TRY(cudaMemsetAsync(d_alpha_ + slot, 0, sizeof(double), st_));
   ED_CUDA_TRY(cudaMemsetAsync(d_beta_ + slot, 0, sizeof(double), st_));
-  ED_CUDA_TRY(cudaStreamSynchronize(st_));
   S.active = true;
   S.converged = false;
   S.iters_seen = 0;
   S.theta = S.theta_prev = 0.0;
-  return rebuild_active();
+  return commit ? rebuild_active() : ED_OK;
 }
 
-void BatchEngine::remove(int slot) {
+void BatchEngine::remove(int slot, bool commit) {
   BSlot& S = slots_[slot];
   if (!S.used) return;
+  const bool was_active = S.active;
   release(S.alloc_off, S.alloc_len);
   S.used = false;
   S.active = false;
-  rebuild_active();
+  if (commit && was_active) rebuild_active();
 }
 
 ed_status BatchEngine::set_mode(int slot, int mode) {

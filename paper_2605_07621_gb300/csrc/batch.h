@@ -106,11 +106,16 @@ class BatchEngine {
   ed_status init(int device, size_t arena_bytes, int max_slots, int max_iter, bool dense);
   // bytes an instance needs in the arena (tables + 3 vectors)
   static ed_status instance_bytes(const ed_model_desc& m, bool dense, size_t* bytes, int64_t* dim);
-  // new instance; its mode is the cached choice for its shape, else CSR
-  ed_status add(const ed_model_desc& m, uint64_t seed, int* slot);
-  void remove(int slot);
-  // fresh start vector (keyed SplitMix64 values, normalised) for an instance
-  ed_status restart(int slot, uint64_t seed);
+  // new instance (active); its mode is the cached choice for its shape, else
+  // the dense form where it has one.  commit = false leaves the device work
+  // lists to one rebuild_active after several adds
+  ed_status add(const ed_model_desc& m, uint64_t seed, int* slot, bool commit = true);
+  // free an instance's arena range; an active instance leaves the device work
+  // lists at once (commit) or at the next rebuild_active
+  void remove(int slot, bool commit = true);
+  // fresh start vector (keyed SplitMix64 values, normalised) for an instance;
+  // commit as for add
+  ed_status restart(int slot, uint64_t seed, bool commit = true);
   // per-instance mode (kModeD64 / kModeD128 fall back to CSR without the
   // dense form); takes effect at the next rebuild_active
   ed_status set_mode(int slot, int mode);

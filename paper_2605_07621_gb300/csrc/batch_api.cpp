@@ -51,7 +51,7 @@ extern "C" ed_status ed_batch_create(const ed_model_desc* models, int n, int fla
   B->slot.resize(n);
   B->off.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    st = B->eng.add(models[i], 20260507ULL, &B->slot[i]);
+    st = B->eng.add(models[i], 20260507ULL, &B->slot[i], false);
     if (st != ED_OK) { delete B; return st; }
     B->off[i + 1] = B->off[i] + dims[i];
     BSlot& S = B->eng.slots()[B->slot[i]];
@@ -59,6 +59,8 @@ extern "C" ed_status ed_batch_create(const ed_model_desc* models, int n, int fla
     st = B->eng.upload_inst(B->slot[i]);
     if (st != ED_OK) { delete B; return st; }
   }
+  st = B->eng.rebuild_active();
+  if (st != ED_OK) { delete B; return st; }
   if (flags == ED_OPS_DEFAULT) {
     // the batch with every instance in each mode, then the tuned choice
     for (int k = 0; k < 3 && st == ED_OK; ++k) st = time_uniform(B, k, &B->tune_ms[k]);
@@ -119,7 +121,8 @@ extern "C" ed_status ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, 
   if (o.mode != ED_LZ_F32) { set_error("the batched Lanczos runs FP32 storage with FP64 reductions (ED_LZ_F32)"); return ED_EUNSUPPORTED; }
   const int max_iter = std::min(o.max_iter, b->eng.max_iter());
   const int K = std::max(1, o.check_every);
-  for (int i = 0; i < b->n; ++i) ED_TRY(b->eng.restart(b->slot[i], o.seed));
+  for (int i = 0; i < b->n; ++i) ED_TRY(b->eng.restart(b->slot[i], o.seed, false));
+  ED_TRY(b->eng.rebuild_active());
   int steps = 0;
   while (b->eng.active_count() > 0 && steps < max_iter) {
     const int k = std::min(K, max_iter - steps);

@@ -81,6 +81,7 @@ static void worker_loop(ed_server* S) {
   while (true) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      int admitted = 0;  // device work lists are rebuilt once for all admissions of this round
       // admission in arrival order while a slot is free and the arena fits
       while (!S->stop && !S->queue.empty()) {
         Request& r = S->reqs[S->queue.front()];
@@ -107,7 +108,7 @@ static void worker_loop(ed_server* S) {
         lk.unlock();
         // CSR or tensor-core form: the choice cached for the shape by a
         // tuned batch of this process, else the dense form
-        ed_status st = S->eng.add(r.m, S->opts.seed, &slot);
+        ed_status st = S->eng.add(r.m, S->opts.seed, &slot, false);
         lk.lock();
         if (st != ED_OK) {
           r.state = 4;
@@ -123,6 +124,26 @@ static void worker_loop(ed_server* S) {
         r.t_admit = Clock::now();
         S->slot_owner[slot] = r.ticket;
         S->free_cache = (int64_t)S->eng.arena_free();
+        ++admitted;
+      }
+      if (admitted > 0) {
+        lk.unlock();
+        const ed_status st = S->eng.rebuild_active();
+        lk.lock();
+        if (st != ED_OK) {
+          const std::string msg = ed_last_error();
+          for (auto& kv : S->reqs)
+            if (kv.second.state == 1) {
+              kv.second.state = 4;
+              kv.second.status = st;
+              kv.second.msg = msg;
+              kv.second.t_done = Clock::now();
+              ++S->failed;
+            }
+          S->stop = true;
+          S->cv_done.notify_all();
+          break;
+        }
       }
       if (S->stop) break;
       if (S->eng.active_count() == 0) {
@@ -158,7 +179,7 @@ static void worker_loop(ed_server* S) {
       r.state = 2;
       r.status = r.converged ? ED_OK : ED_ENOCONV;
       r.t_done = Clock::now();
-      S->eng.remove(slot);
+      S->eng.remove(slot, false);
       r.slot = -1;
       S->latencies.push_back(std::chrono::duration<double>(r.t_done - r.t_submit).count());
       ++S->completed;
