@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "apply3.cuh"  // I128, from_fixed128
 #include "tc.cuh"
 
 namespace edk {
@@ -443,43 +444,97 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       if (s_abort) atomicExch(err, 1);
     }
   } else {
-    // ---- epilogue: thread = one output row, 64 columns in FP64
+    // ---- epilogue: thread = one output row.  The 8 digit-order sums S_g of
+    // a chunk are exact integers below 2^24 held in FP32; per column they
+    // become one 128-bit integer T = sum_g S_g 2^(42 - 6g) (orders 0-3 and
+    // 4-7 summed in two 64-bit integers first) on the integer pipe, rounded
+    // once to FP64 by bit manipulation (C = T 2^(E_A + E_B - 52)).  With
+    // more than one K chunk the chunks' rounded values add in FP64.
     const int row = warp * 32 + lane;
-    double acc[kOzBN];
+    const int i = m0 + row;
+    const bool rv = i < P.M;
+    const int ea = rv ? P.ea[i] : 0;
+    double* crow = rv ? (P.cbase == 1 ? y + P.coff : P.C) + (long long)i * P.ldc : nullptr;
+    const unsigned tl = tmem + ((unsigned)(warp * 32) << 16);
+    // T of the 8 columns 8q .. 8q + 7 of the tile
+    auto group = [&](int q, I128* T) {
+      long long H[8], L[8];
 #pragma unroll
-    for (int j = 0; j < kOzBN; ++j) acc[j] = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
+      for (int j = 0; j < 8; ++j) H[j] = L[j] = 0;
+#pragma unroll
+      for (int g = 0; g < kOzDigits; ++g) {
+        float v[8];
+        tc::tmem_ld8(tl + (unsigned)(g * kOzBN + 8 * q), v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const long long sg = (long long)__float2int_rn(v[j]);
+          if (g < 4) H[j] += sg << (6 * (3 - g));
+          else L[j] += sg << (6 * (7 - g));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        I128 h, l;
+        h.lo = (unsigned long long)H[j] << 24;
+        h.hi = H[j] >> 40;
+        l.lo = (unsigned long long)L[j];
+        l.hi = L[j] >> 63;
+        T[j] = h + l;
+      }
+    };
+    auto wait_chunk = [&](int c) -> bool {
       bool ok = false;
-      for (long long i = 0; i < kOzSpin && !ok; ++i) {
+      for (long long it = 0; it < kOzSpin && !ok; ++it) {
         ok = tc::mbar_try(acc_full, c & 1);
         if (!ok && s_abort) break;
       }
-      if (!ok) { s_abort = 1; break; }
-      tc::tc_fence_after();
+      if (!ok) s_abort = 1;
+      return ok;
+    };
+    if (nchunk == 1) {
+      if (wait_chunk(0)) {
+        tc::tc_fence_after();
+#pragma unroll 1
+        for (int q = 0; q < kOzBN / 8; ++q) {
+          I128 T[8];
+          group(q, T);
 #pragma unroll
-      for (int g = 0; g < kOzDigits; ++g) {
-        const double sc = pow2(-kOzBits * g);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float v[32];
-          tc::tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(g * kOzBN + 32 * h), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc[32 * h + j] = fma((double)v[j], sc, acc[32 * h + j]);
+          for (int j = 0; j < 8; ++j) {
+            const int col = n0 + 8 * q + j;
+            if (rv && col < P.N) {
+              const double v = from_fixed128(T[j], ea + P.eb[col] - 52);
+              crow[col] = P.acc ? crow[col] + v : v;
+            }
+          }
         }
+        tc::tc_fence_before();
+        tc::mbar_arrive(acc_empty);
       }
-      tc::tc_fence_before();
-      tc::mbar_arrive(acc_empty);
-    }
-    const int i = m0 + row;
-    if (!s_abort && i < P.M) {
-      const int ea = P.ea[i];
-      double* crow = (P.cbase == 1 ? y + P.coff : P.C) + (long long)i * P.ldc;
+    } else {
+      double acc[kOzBN];
 #pragma unroll
-      for (int j = 0; j < kOzBN; ++j) {
-        const int col = n0 + j;
-        if (col < P.N) {
-          const double v = acc[j] * pow2(ea + P.eb[col] - 10);
-          crow[col] = P.acc ? crow[col] + v : v;
+      for (int j = 0; j < kOzBN; ++j) acc[j] = 0.0;
+      for (int c = 0; c < nchunk; ++c) {
+        if (!wait_chunk(c)) break;
+        tc::tc_fence_after();
+#pragma unroll
+        for (int q = 0; q < kOzBN / 8; ++q) {
+          I128 T[8];
+          group(q, T);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[8 * q + j] += from_fixed128(T[j], -42);
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(acc_empty);
+      }
+      if (!s_abort && rv) {
+#pragma unroll
+        for (int j = 0; j < kOzBN; ++j) {
+          const int col = n0 + j;
+          if (col < P.N) {
+            const double v = acc[j] * pow2(ea + P.eb[col] - 10);
+            crow[col] = P.acc ? crow[col] + v : v;
+          }
         }
       }
     }
