@@ -11,6 +11,20 @@
 //     its row sums and, below the diagonal, its column sums to slots of its
 //     own that a second kernel adds up, so each step reads and writes the
 //     stored triangle once.
+//     Blocked form (the entanglement spectrum's Gram matrices; Golub and
+//     Van Loan Sec. 8.3, the panel scheme of LAPACK's dsytrd/dlatrd): the
+//     reflectors of a panel of kTriNb columns are formed against the
+//     panel's starting matrix with the panel's pending updates applied on
+//     the fly (column c, and p = A v - V (W^T v) - W (V^T v)); after the
+//     panel the trailing matrix takes A -= V W^T + W V^T in one
+//     FP64-accurate tensor-core product (rank 2 kTriNb, lower-triangle
+//     tiles).  The product A v, the whole cost of the reduction, reads a
+//     float-float copy of the panel's starting matrix (48 significant bits,
+//     error-free products and sums on the FP32 pipe inside 64 x 64 units,
+//     FP64 across units): on this GPU FP64 arithmetic runs about 70 times
+//     slower than FP32, and the float-float pass is bound by HBM instead.
+//     Per column three kernels: the column and its reflector (k_pcol), the
+//     product (k_symv), its sums and the pending terms (k_psum2).
 //  2. The eigenvalues of the tridiagonal matrix by implicit QL steps with
 //     shifts and deflation, on the host, one thread per matrix.
 #include <algorithm>
@@ -18,6 +32,7 @@
 #include <vector>
 
 #include "eigsym.h"
+#include "tc.cuh"
 
 namespace edk {
 namespace {
@@ -186,6 +201,572 @@ __global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e
   }
 }
 
+// ---- blocked reduction: panel kernels.  WV row r holds w_0..w_{nb-1} at
+// columns 0..nb-1 and v_0..v_{nb-1} at nb..2nb-1 (the panel's reflectors so
+// far, zero elsewhere); NVW holds the same with the halves swapped and
+// negated (the operands of the trailing update).  Within a panel the
+// products A v read a float-float copy F of the panel's starting matrix:
+// a = hi + lo with two FP32 values (48 significant bits), scaled by a power
+// of two 2^sh that brings the largest entry into [1/2, 1), so that the
+// products run on the FP32 pipe (this GPU's FP64 pipe is about 70 times
+// slower) with error-free products (FMA) and sums (Knuth's TwoSum) inside a
+// 64 x 64 unit, and every unit's sums meet in FP64.
+constexpr int kNb = kTriNb, kKw = 2 * kTriNb;
+constexpr int kU = 64;             // edge of the product's units
+constexpr int kSvWarps = 2;        // warps (units in flight) per CTA of the product
+constexpr int kTs = 34;            // row stride (float2) of its staging tiles: 16-byte aligned rows
+constexpr int kPcolCtas = 128;     // most CTAs of k_pcol (partial-sum slots)
+constexpr int kRowCtas = 4096;     // most CTAs of k_psum2 (partial-sum slots)
+constexpr int kAmaxCtas = 1024;    // most CTAs of k_amax
+constexpr int kPr = 8;             // rows per warp and step of k_pcol
+constexpr int kPsT = 16;           // threads per row of k_psum2
+static_assert(kPcolCtas == 128 && kRowCtas == 4096 && kAmaxCtas == 1024 && kU == 64,
+              "tridiag_blocked_work_doubles counts these slots");
+
+// a * 2^sh as hi + lo: hi = the leading 24 significant bits (truncated), lo =
+// the next 29 rounded to 24, so hi + lo is within 2^-48 |a 2^sh|; built from
+// the FP64 bit fields on the integer pipe.  Magnitudes below 2^-126 (after
+// scaling) become zero; the caller keeps the scaled magnitude below 2^127.
+__device__ __forceinline__ float2 split_scaled(double a, int sh) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned s = (unsigned)(u >> 63) << 31;
+  const int E = (int)((u >> 52) & 0x7ffu);
+  if (E == 0) return make_float2(0.f, 0.f);  // zero or FP64 subnormal
+  const int e = E - 1023 + sh;
+  if (e < -126) return make_float2(0.f, 0.f);
+  const unsigned long long M = u & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)(M >> 29));
+  const unsigned long long R = M & 0x1FFFFFFFull;  // the remaining 29 bits, unit 2^(e - 52)
+  if (R == 0) return make_float2(hi, 0.f);
+  const int nb = 64 - __clzll((long long)R);  // bit length, 1..29
+  int el = e - 53 + nb;                       // exponent of R's leading bit
+  unsigned frac;
+  if (nb > 24) {
+    const int d = nb - 24;
+    unsigned long long q = (R + (1ull << (d - 1))) >> d;
+    if (q >> 24) {
+      q >>= 1;
+      ++el;
+    }
+    frac = (unsigned)q & 0x7FFFFFu;
+  } else {
+    frac = (unsigned)(R << (24 - nb)) & 0x7FFFFFu;
+  }
+  if (el < -126) return make_float2(hi, 0.f);
+  return make_float2(hi, __uint_as_float(s | ((unsigned)(el + 127) << 23) | frac));
+}
+
+// (sh, sl) += (ah + al)(bh + bl): ah bh split exactly into p + e (FMA), p
+// added to sh by TwoSum, the rounding error, e and the cross terms into sl
+// (al bl, below 2^-48 of the product, is dropped).  The _rn intrinsics keep
+// the compiler from contracting or reordering the error-free steps.
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = fmaf(ah, bh, -p);
+  const float s = __fadd_rn(sh, p);
+  const float z = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, fmaf(ah, bl, fmaf(al, bh, e))));
+}
+
+__device__ inline unsigned long long warp_umax(unsigned long long x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+// largest |A[r][c]| over the trailing triangle r0 <= c <= r < m, per CTA, as
+// FP64 bit patterns without the sign (their unsigned order is the order of
+// the magnitudes); one warp per row
+__global__ void __launch_bounds__(256) k_amax(const double* __restrict__ A, int m, int r0,
+                                              unsigned long long* __restrict__ amx) {
+  __shared__ unsigned long long red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long ld = m;
+  unsigned long long x = 0;
+  for (int r = r0 + blockIdx.x * 8 + warp; r < m; r += gridDim.x * 8) {
+    const double* row = A + (long long)r * ld;
+    for (int c = r0 + lane; c <= r; c += 32) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(row[c]) & 0x7FFFFFFFFFFFFFFFull;
+      x = b > x ? b : x;
+    }
+  }
+  x = warp_umax(x);
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) x = red[w] > x ? red[w] : x;
+    amx[blockIdx.x] = x;
+  }
+}
+
+// the float-float copy F = split(A 2^sh) of the trailing triangle (row
+// stride ldF); sh (the
+// same in every CTA, written to *shp by CTA 0) brings the largest magnitude
+// into [1/2, 1)
+__global__ void __launch_bounds__(256) k_pconv(const double* __restrict__ A, float2* __restrict__ F, long long ldF,
+                                               int m, int r0, const unsigned long long* __restrict__ amx, int na,
+                                               int* shp) {
+  __shared__ int s_sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    unsigned long long x = 0;
+    for (int b = lane; b < na; b += 32) x = amx[b] > x ? amx[b] : x;
+    x = warp_umax(x);
+    if (lane == 0) {
+      s_sh = x == 0 ? 0 : 1022 - (int)(x >> 52);
+      if (blockIdx.x == 0) *shp = s_sh;
+    }
+  }
+  __syncthreads();
+  const int sh = s_sh;
+  const long long ld = m;
+  for (int r = r0 + blockIdx.x * 8 + warp; r < m; r += gridDim.x * 8) {
+    const double* row = A + (long long)r * ld;
+    float2* out = F + (long long)r * ldF;
+    for (int c = r0 + lane; c <= r; c += 32) out[c] = split_scaled(row[c], sh);
+  }
+}
+
+// column c of the matrix with the panel's pending updates, rows c+1..m-1,
+// into v (and its scaled split into vf); one warp per kPr rows at a time,
+// lanes over the panel's terms.  Column j - 1 of the panel (the previous
+// reflector) is not stored yet: its w' = beta' p - K' v' (from the previous
+// column's p, v, beta and K) is formed here, row by row, and stored with v'
+// as it is used.  Per CTA: the partial sums W^T x (slots 0..nb-1), V^T x
+// (slots nb..2nb-1) over rows c+1.. and the sum of squares below row c+1
+// (slot 2nb); the last CTA to finish (a ticket on *ctr) adds them up in a
+// fixed order and forms the reflector of column c: beta_c, d_c, e_c, v[c+1]
+// (and vf[c+1]) and, for j > 0, tu = (W^T v, V^T v), where v differs from x
+// only in row c+1 (v = x - alpha e_{c+1}).
+__global__ void __launch_bounds__(256) k_pcol(const double* __restrict__ A, int m, int c, int j,
+                                              double* __restrict__ WV, double* __restrict__ v,
+                                              float2* __restrict__ vf, const int* __restrict__ shp,
+                                              const double* __restrict__ p, double* beta, const double* Kp,
+                                              double* __restrict__ cp, unsigned* ctr, double* d, double* e,
+                                              double* __restrict__ tu) {
+  __shared__ double acc[8][kKw + 1];
+  __shared__ double tot[kKw + 1];
+  __shared__ double s_alpha, s_vw;
+  __shared__ unsigned s_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sh = *shp;
+  const int jp = j - 1;  // the pending column formed here (none for j = 0)
+  const double bp = j > 0 ? beta[c - 1] : 0.0, Kq = j > 0 ? *Kp : 0.0;
+  const double vpc = j > 0 ? v[c] : 0.0, wpc = j > 0 ? bp * p[c] - Kq * vpc : 0.0;  // v'_c, w'_c
+  const double* rc = WV + (long long)c * kKw;
+  double w0 = lane < jp ? rc[lane] : 0.0, w1 = lane + 32 < jp ? rc[lane + 32] : 0.0;
+  double v0 = lane < jp ? rc[kNb + lane] : 0.0, v1 = lane + 32 < jp ? rc[kNb + lane + 32] : 0.0;
+  if (lane == jp) {
+    w0 = wpc;
+    v0 = vpc;
+  }
+  if (lane + 32 == jp) {
+    w1 = wpc;
+    v1 = vpc;
+  }
+  if (j > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    WV[(long long)c * kKw + jp] = wpc;
+    WV[(long long)c * kKw + kNb + jp] = vpc;
+  }
+  const long long ld = m;
+  double s2 = 0.0, dw0 = 0.0, dw1 = 0.0, dv0 = 0.0, dv1 = 0.0;
+  for (int rb = c + 1 + (blockIdx.x * 8 + warp) * kPr; rb < m; rb += gridDim.x * 8 * kPr) {
+    double a[kPr], t[kPr], rw0[kPr], rw1[kPr], rv0[kPr], rv1[kPr], wq[kPr], vq[kPr];
+#pragma unroll
+    for (int q = 0; q < kPr; ++q) {
+      const int r = rb + q;
+      const bool in = r < m;
+      const double* row = WV + (long long)(in ? r : c) * kKw;
+      a[q] = in ? A[(long long)r * ld + c] : 0.0;
+      rw0[q] = in && lane < jp ? row[lane] : 0.0;
+      rv0[q] = in && lane < jp ? row[kNb + lane] : 0.0;
+      rw1[q] = in && lane + 32 < jp ? row[lane + 32] : 0.0;
+      rv1[q] = in && lane + 32 < jp ? row[kNb + lane + 32] : 0.0;
+      vq[q] = j > 0 && in ? v[r] : 0.0;  // v'_r, read before this kernel overwrites it
+      wq[q] = j > 0 && in ? bp * p[r] - Kq * vq[q] : 0.0;
+      if (lane == jp) {
+        rw0[q] = wq[q];
+        rv0[q] = vq[q];
+      }
+      if (lane + 32 == jp) {
+        rw1[q] = wq[q];
+        rv1[q] = vq[q];
+      }
+      t[q] = rv0[q] * w0 + rw0[q] * v0 + rv1[q] * w1 + rw1[q] * v1;
+    }
+    if (j > 0) {
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < kPr; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPr; ++q) {
+      const int r = rb + q;
+      if (r >= m) break;
+      const double x = a[q] - t[q];
+      if (lane == 0) {
+        if (j > 0) {
+          WV[(long long)r * kKw + jp] = wq[q];
+          WV[(long long)r * kKw + kNb + jp] = vq[q];
+        }
+        v[r] = x;
+        vf[r] = split_scaled(x, sh);
+        if (r > c + 1) s2 += x * x;
+      }
+      dw0 += rw0[q] * x;
+      dv0 += rv0[q] * x;
+      dw1 += rw1[q] * x;
+      dv1 += rv1[q] * x;
+    }
+  }
+  acc[warp][lane] = dw0;
+  acc[warp][lane + 32] = dw1;
+  acc[warp][kNb + lane] = dv0;
+  acc[warp][kNb + lane + 32] = dv1;
+  if (lane == 0) acc[warp][kKw] = s2;
+  __syncthreads();
+  for (int k = threadIdx.x; k <= kKw; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += acc[w][k];
+    cp[(long long)blockIdx.x * (kKw + 1) + k] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last CTA: the reflector of column c; thread (k, half) adds slot k
+  // of every other CTA's partials, then the halves meet
+  {
+    const int k = threadIdx.x & (kKw - 1), hf = threadIdx.x >> 7;
+    double s = 0.0;
+#pragma unroll 16
+    for (int b = hf; b < (int)gridDim.x; b += 2) s += cp[(long long)b * (kKw + 1) + k];
+    acc[hf][k] = s;
+    if (warp == 0) {  // slot 2 nb (the sum of squares)
+      double q = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) q += cp[(long long)b * (kKw + 1) + kKw];
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (lane == 0) tot[kKw] = q;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kKw) tot[threadIdx.x] = acc[0][threadIdx.x] + acc[1][threadIdx.x];
+  if (warp == 0) {  // sum_i V[c,i] W[c,i] (the diagonal's pending update)
+    double t = 0.0;
+    if (lane < j) t += rc[kNb + lane] * rc[lane];
+    if (lane + 32 < j) t += rc[kNb + lane + 32] * rc[lane + 32];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_vw = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *ctr = 0u;
+    d[c] = A[(long long)c * ld + c] - 2.0 * s_vw;
+    const double tail = tot[kKw];
+    const double x0 = v[c + 1];
+    const double nrm = sqrt(x0 * x0 + tail);
+    double alpha = 0.0;
+    if (tail == 0.0) {  // nothing to annihilate
+      e[c] = x0;
+      beta[c] = 0.0;
+    } else {
+      alpha = x0 >= 0.0 ? -nrm : nrm;
+      v[c + 1] = x0 - alpha;
+      vf[c + 1] = split_scaled(x0 - alpha, sh);
+      beta[c] = 1.0 / (nrm * (nrm + fabs(x0)));
+      e[c] = alpha;
+    }
+    s_alpha = alpha;
+  }
+  __syncthreads();
+  if (j > 0 && threadIdx.x < kKw) tu[threadIdx.x] = tot[threadIdx.x] - s_alpha * WV[(long long)(c + 1) * kKw + threadIdx.x];
+}
+
+// unit t of the triangle, numbered row by row: (I, J), J <= I
+__device__ __forceinline__ void unit_ij(long long t, int& I, int& J) {
+  long long i = (long long)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  I = (int)i;
+  J = (int)(t - i * (i + 1) / 2);
+}
+
+// (sh, sl) += (bh, bl) for two float-float sums (TwoSum of the leading parts)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+  const float s = __fadd_rn(sh, bh);
+  const float z = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(bh, z));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, bl));
+}
+
+constexpr long long kSvSpin = 1LL << 24;  // polls of an mbarrier before k_symv gives up
+
+// partial sums of p = A v over the trailing triangle from the float-float
+// copy.  Units of 64 x 64 (I, J), J <= I, start at row and column u0 (r0
+// rounded down to even, so that every box starts on a 16-byte boundary; v is
+// zero below r0) and are numbered row by row; one warp per unit, as 2 x 2
+// sub-tiles of 32 x 32, each brought into shared memory by one TMA box of
+// 32 rows x 34 columns (the two extra columns give a 272-byte row pitch, free
+// of bank conflicts), two buffers per warp so that the next sub-tile (across
+// units) is in flight while one is summed.  Lane = column for the column sums
+// (a_ij v_i, kept in registers over the unit's rows), lane = row for the row
+// sums (a_ij v_j); two independent float-float chains each.  Diagonal
+// entries count once, for their row.  Unit (I, J) writes its row sums to slot
+// J and its column sums to slot TU + I of `part` (slot s, row i at
+// part[s * m + i]) in FP64; the sums are in units of 2^(2 sh).
+__global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ CUtensorMap tmF, int m, int r0,
+                                                        int u0, const float2* __restrict__ vf,
+                                                        double* __restrict__ part, int TU, long long nunits,
+                                                        int* err) {
+  __shared__ __align__(128) float2 tile[kSvWarps][2][32][kTs];
+  __shared__ __align__(16) float2 vs[kSvWarps][2 * kU];  // the unit's row values, then its column values
+  __shared__ __align__(8) uint64_t bar[kSvWarps][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long ld = m;
+  const long long t0 = (long long)blockIdx.x * kSvWarps + w, nw = (long long)gridDim.x * kSvWarps;
+  if (lane == 0) {
+    tc::mbar_init(&bar[w][0], 1);
+    tc::mbar_init(&bar[w][1], 1);
+    tc::fence_mbar_init();
+  }
+  __syncwarp();
+  // sub-tile k of this warp: unit t0 + (k / 4) nw, s = k % 4 -> column half
+  // h = s / 2, row half g = s % 2; false if it holds nothing to sum
+  auto present = [&](long long k, int& I, int& J) {
+    const long long t = t0 + (k >> 2) * nw;
+    if (t >= nunits) return false;
+    const int s = (int)(k & 3), h = s >> 1, g = s & 1;
+    unit_ij(t, I, J);
+    return !(I == J && g < h) && u0 + I * kU + 32 * g < m;
+  };
+  const uint64_t pol = tc::l2_evict_first();  // F streams through once per column; the small buffers stay in L2
+  auto issue = [&](long long k) {
+    int I, J;
+    if (!present(k, I, J) || lane != 0) return;
+    const int s = (int)(k & 3), h = s >> 1, g = s & 1;
+    uint64_t* b = &bar[w][k & 1];
+    tc::mbar_expect_tx(b, 32 * kTs * (unsigned)sizeof(float2));
+    tc::tma_load_2d_hint(tile[w][k & 1], &tmF, u0 + J * kU + 32 * h, u0 + I * kU + 32 * g, b, pol);
+  };
+  issue(0);
+  issue(1);
+  unsigned phases = 0u;  // bit b: parity of the next phase of buffer b
+  int I = 0, J = 0, ib = 0, jb = 0;
+  bool diag = false;
+  float rh0 = 0.f, rl0 = 0.f, rh1 = 0.f, rl1 = 0.f;  // row sums of rows ib + lane, ib + 32 + lane
+  float ch = 0.f, cl = 0.f;                          // column sums of column jb + 32 h + lane
+  for (long long k = 0;; ++k) {
+    const long long t = t0 + (k >> 2) * nw;
+    if (t >= nunits) break;
+    const int s = (int)(k & 3), h = s >> 1, g = s & 1;
+    if (s == 0) {
+      unit_ij(t, I, J);
+      diag = I == J;
+      ib = u0 + I * kU;
+      jb = u0 + J * kU;
+      __syncwarp();
+      for (int q = lane; q < kU; q += 32) {
+        const int a = ib + q, b = jb + q;
+        vs[w][q] = a >= r0 && a < m ? vf[a] : make_float2(0.f, 0.f);
+        vs[w][kU + q] = b >= r0 && b < m ? vf[b] : make_float2(0.f, 0.f);
+      }
+      rh0 = rl0 = rh1 = rl1 = 0.f;
+      __syncwarp();
+    }
+    if (g == 0) ch = cl = 0.f;
+    const int j = jb + 32 * h + lane;
+    int Ik, Jk;
+    if (present(k, Ik, Jk)) {
+      if (!tc::mbar_wait(&bar[w][k & 1], (phases >> (k & 1)) & 1u, kSvSpin)) {
+        // give up: record it, let the other buffer's copy land, stop
+        if (lane == 0) atomicExch(err, 3);
+        int I2, J2;
+        if (present(k + 1, I2, J2)) tc::mbar_wait(&bar[w][(k + 1) & 1], (phases >> ((k + 1) & 1)) & 1u, kSvSpin);
+        return;
+      }
+      phases ^= 1u << (k & 1);
+      const float2(*buf)[kTs] = tile[w][k & 1];
+      const float2* xr = &vs[w][32 * g];
+      const float2* xc = &vs[w][kU + 32 * h];
+      float c2h = 0.f, c2l = 0.f, r2h = 0.f, r2l = 0.f, r3h = 0.f, r3l = 0.f;
+      if (!(diag && g == h)) {
+#pragma unroll
+        for (int li = 0; li < 32; li += 2) {
+          const float2 a0 = buf[li][lane], x0 = xr[li];
+          const float2 a1 = buf[li + 1][lane], x1 = xr[li + 1];
+          df_fma(ch, cl, a0.x, a0.y, x0.x, x0.y);
+          df_fma(c2h, c2l, a1.x, a1.y, x1.x, x1.y);
+        }
+#pragma unroll
+        for (int q = 0; q < 32; q += 2) {
+          const float4 a2 = *reinterpret_cast<const float4*>(&buf[lane][q]);
+          const float4 x2 = *reinterpret_cast<const float4*>(&xc[q]);
+          df_fma(r2h, r2l, a2.x, a2.y, x2.x, x2.y);
+          df_fma(r3h, r3l, a2.z, a2.w, x2.z, x2.w);
+        }
+      } else {  // diagonal sub-tile: entry (li, q) is stored for q <= li only
+#pragma unroll 4
+        for (int li = 0; li < 32; ++li) {
+          if (li > lane) {
+            const float2 a0 = buf[li][lane], x0 = xr[li];
+            df_fma(ch, cl, a0.x, a0.y, x0.x, x0.y);
+          }
+        }
+#pragma unroll 4
+        for (int q = 0; q < 32; ++q) {
+          if (q <= lane) {
+            const float2 a0 = buf[lane][q], x0 = xc[q];
+            df_fma(r2h, r2l, a0.x, a0.y, x0.x, x0.y);
+          }
+        }
+      }
+      df_add(ch, cl, c2h, c2l);
+      df_add(r2h, r2l, r3h, r3l);
+      if (g == 0)
+        df_add(rh0, rl0, r2h, r2l);
+      else
+        df_add(rh1, rl1, r2h, r2l);
+    }
+    if (g == 1 && j >= r0 && j < m) part[(long long)(TU + I) * ld + j] = (double)ch + (double)cl;
+    if (s == 3) {
+      if (ib + lane >= r0 && ib + lane < m) part[(long long)J * ld + ib + lane] = (double)rh0 + (double)rl0;
+      if (ib + 32 + lane < m) part[(long long)J * ld + ib + 32 + lane] = (double)rh1 + (double)rl1;
+    }
+    __syncwarp();
+    issue(k + 2);
+  }
+}
+
+// p[i] for rows i >= r0: the unit slots that k_symv wrote (row slots 0..I(i),
+// column slots TU + I(i) .. TU + Tn - 1, units from u0), scaled back by
+// 2^(-2 sh), minus the panel's pending terms V (W^T v) + W (V^T v); kPsT
+// threads per row.  Per CTA: the partial sum of p.v; the last CTA to finish
+// (a ticket on *ctr) adds them in a fixed order into K = beta^2 p.v / 2 (*Kp),
+// which makes w = beta p - K v.
+__global__ void __launch_bounds__(256) k_psum2(const double* __restrict__ part, int m, int r0, int u0, int TU, int Tn,
+                                               const int* __restrict__ shp, const double* __restrict__ WV,
+                                               const double* __restrict__ tu, int j, const double* __restrict__ v,
+                                               double* __restrict__ p, double* __restrict__ pvp,
+                                               const double* beta, int c, unsigned* ctr, double* Kp) {
+  __shared__ double red[33];
+  __shared__ unsigned s_last;
+  const int q = threadIdx.x & (kPsT - 1);
+  const int sh = *shp;
+  const long long ld = m;
+  double pv = 0.0;
+  constexpr int rows_cta = 256 / kPsT;
+  for (int base = r0 + blockIdx.x * rows_cta; base < m; base += gridDim.x * rows_cta) {
+    const int i = base + threadIdx.x / kPsT;
+    double s = 0.0, corr = 0.0;
+    if (i < m) {
+      const int Ii = (i - u0) / kU;
+#pragma unroll 8
+      for (int J = q; J <= Ii; J += kPsT) s += part[(long long)J * ld + i];
+#pragma unroll 8
+      for (int I = Ii + q; I < Tn; I += kPsT) s += part[(long long)(TU + I) * ld + i];
+      const double* row = WV + (long long)i * kKw;
+#pragma unroll 4
+      for (int k = q; k < j; k += kPsT) corr += row[kNb + k] * tu[k] + row[k] * tu[kNb + k];
+    }
+    for (int o = kPsT / 2; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      corr += __shfl_xor_sync(0xffffffffu, corr, o);
+    }
+    if (i < m && q == 0) {
+      const double pi = ldexp(ldexp(s, -sh), -sh) - corr;
+      p[i] = pi;
+      pv += pi * v[i];
+    }
+  }
+  pv = block_sum(pv, red);
+  if (threadIdx.x == 0) pvp[blockIdx.x] = pv;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += pvp[b];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double b = beta[c];
+    *Kp = 0.5 * b * b * s;
+    *ctr = 0u;
+  }
+}
+
+// w = beta p - K v over rows c+1..m-1 (p = A v without beta), stored with v
+// as column j of the panel (the panel's last column; the others are stored
+// by the next column's k_pcol)
+__global__ void __launch_bounds__(256) k_pw(int m, int c, int j, const double* __restrict__ v,
+                                            const double* __restrict__ p, const double* Kp, const double* beta,
+                                            double* __restrict__ WV) {
+  const double b = beta[c], K = *Kp;
+  for (int r = c + 1 + blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    const double vr = v[r];
+    WV[(long long)r * kKw + j] = b * p[r] - K * vr;
+    WV[(long long)r * kKw + kNb + j] = vr;
+  }
+}
+
+__device__ inline double block_max(double x, double* red) {
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    x = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (l == 0) red[32] = x;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// after the panel: column j of v scaled by 2^k and of w by 2^-k (their
+// product unchanged) so that their largest magnitudes meet, and the negated
+// swapped copy NVW; the trailing product slices each operand row with one
+// exponent across all the panel's v and w, and this keeps either half from
+// losing its low digits to the other.  One CTA per column.
+__global__ void __launch_bounds__(256) k_pbal(int m, int k0, double* __restrict__ WV, double* __restrict__ NVW) {
+  __shared__ double red[33];
+  const int j = blockIdx.x, c = k0 + j;
+  double mv = 0.0, mw = 0.0;
+  for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
+    mv = fmax(mv, fabs(WV[(long long)r * kKw + kNb + j]));
+    mw = fmax(mw, fabs(WV[(long long)r * kKw + j]));
+  }
+  mv = block_max(mv, red);
+  mw = block_max(mw, red);
+  int k = 0;
+  if (mv > 0.0 && mw > 0.0) {
+    int ev, ew;
+    frexp(mv, &ev);
+    frexp(mw, &ew);
+    k = (ew - ev) / 2;
+  }
+  const double sv = ldexp(1.0, k), sw = ldexp(1.0, -k);
+  for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
+    double* row = WV + (long long)r * kKw;
+    double* nrow = NVW + (long long)r * kKw;
+    const double vi = row[kNb + j] * sv, wi = row[j] * sw;
+    row[kNb + j] = vi;
+    row[j] = wi;
+    nrow[j] = -vi;
+    nrow[kNb + j] = -wi;
+  }
+}
+
 }  // namespace
 
 ed_status tridiag_reduce(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st,
@@ -230,6 +811,122 @@ ed_status tridiag_reduce(double* A, int m, double* work, double* d_host, double*
   ED_CUDA_TRY(cudaGetLastError());
   ED_CUDA_TRY(cudaMemcpyAsync(d_host, d, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (m >= 2) ED_CUDA_TRY(cudaMemcpyAsync(e_host, e, (size_t)(m - 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return ED_OK;
+}
+
+std::vector<TriPanel> tridiag_panels(int m) {
+  std::vector<TriPanel> out;
+  for (int k0 = 0; k0 < m - 2; k0 += kTriNb) {
+    TriPanel t;
+    t.k0 = k0;
+    t.jb = std::min(kTriNb, m - 2 - k0);
+    t.t0 = k0 + t.jb;
+    out.push_back(t);
+  }
+  return out;
+}
+
+ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st,
+                                 int sms, const TriBlocked& tb) {
+  if (m < 3) return tridiag_reduce(A, m, work, d_host, e_host, st, sms);
+  const int TU = (m + kU - 1) / kU;
+  double* v = work;
+  double* p = work + m;
+  double* beta = work + 2 * m;
+  double* d = work + 3 * m;
+  double* e = work + 4 * m;
+  float2* vf = reinterpret_cast<float2*>(work + 5 * m);
+  double* part = work + 6 * m;                                   // 2 TU slots of m
+  double* cp = part + 2LL * TU * m;                              // k_pcol partials (kPcolCtas x (2 nb + 1))
+  double* tu = cp + (long long)kPcolCtas * (kKw + 1);            // W^T v, V^T v (2 nb)
+  double* pvp = tu + kKw;                                        // p.v partials (kRowCtas)
+  auto* amx = reinterpret_cast<unsigned long long*>(pvp + kRowCtas);  // kAmaxCtas
+  double* Kp = reinterpret_cast<double*>(amx + kAmaxCtas);       // K of the latest column
+  int* shp = reinterpret_cast<int*>(Kp + 1);                     // the panel's scale exponent
+  unsigned* ctr = reinterpret_cast<unsigned*>(Kp + 2);           // tickets of k_pcol and k_psum2
+  ED_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st));
+  auto cdiv = [](long long a, long long b) { return (a + b - 1) / b; };
+  const std::vector<TriPanel> pan = tridiag_panels(m);
+  for (size_t q = 0; q < pan.size(); ++q) {
+    const TriPanel& P = pan[q];
+    ED_CUDA_TRY(cudaMemsetAsync(tb.WV + (long long)P.k0 * kKw, 0, (size_t)(m - P.k0) * kKw * sizeof(double), st));
+    ED_CUDA_TRY(cudaMemsetAsync(tb.NVW + (long long)P.k0 * kKw, 0, (size_t)(m - P.k0) * kKw * sizeof(double), st));
+    // float-float copy of the panel's trailing triangle (rows and columns >= k0 + 1)
+    {
+      const int r0 = P.k0 + 1;
+      const int ga = (int)std::max(1LL, std::min((long long)kAmaxCtas, cdiv(m - r0, 8)));
+      k_amax<<<ga, 256, 0, st>>>(A, m, r0, amx);
+      const int gc = (int)std::max(1LL, std::min((long long)sms * 8, cdiv(m - r0, 8)));
+      k_pconv<<<gc, 256, 0, st>>>(A, tb.F, tb.ldF, m, r0, amx, ga, shp);
+    }
+    for (int j = 0; j < P.jb; ++j) {
+      const int c = P.k0 + j;
+      const int n = m - c - 1;  // rows and columns of the product, from c + 1
+      const int g1 = (int)std::max(1LL, std::min((long long)kPcolCtas, cdiv(n, 8 * kPr)));
+      k_pcol<<<g1, 256, 0, st>>>(A, m, c, j, tb.WV, v, vf, shp, p, beta, Kp, cp, ctr, d, e, tu);
+      const int u0 = (c + 1) & ~1;  // the units' origin: even, so that the boxes start 16-byte aligned
+      const long long Tn = cdiv(m - u0, kU), nu = Tn * (Tn + 1) / 2;
+      const int gs = (int)std::max(1LL, std::min((long long)sms * 6, cdiv(nu, kSvWarps)));
+      k_symv<<<gs, 32 * kSvWarps, 0, st>>>(tb.tmF, m, c + 1, u0, vf, part, TU, nu, tb.err);
+      const int g4 = (int)std::max(1LL, std::min((long long)kRowCtas, cdiv(n, 256 / kPsT)));
+      k_psum2<<<g4, 256, 0, st>>>(part, m, c + 1, u0, TU, (int)Tn, shp, tb.WV, tu, j, v, p, pvp, beta, c, ctr + 1,
+                                  Kp);
+    }
+    {
+      const int c = P.k0 + P.jb - 1;
+      const int g5 = (int)std::max(1LL, std::min((long long)sms * 2, cdiv(m - c - 1, 256)));
+      k_pw<<<g5, 256, 0, st>>>(m, c, P.jb - 1, v, p, Kp, beta, tb.WV);
+    }
+    k_pbal<<<P.jb, 256, 0, st>>>(m, P.k0, tb.WV, tb.NVW);
+    // trailing matrix (rows and columns >= t0): A -= V W^T + W V^T
+    ED_TRY(oz_slice(tb.oz, tb.d_jobs + 2 * q, 2, 2LL * (m - P.t0), false, nullptr, st));
+    ED_TRY(oz_gemm(tb.oz, tb.d_probs + q, 1, oz_tiles(m - P.t0, m - P.t0, 1), nullptr, st));
+  }
+  k_tail<<<1, 32, 0, st>>>(A, m, d, e);
+  ED_CUDA_TRY(cudaGetLastError());
+  ED_CUDA_TRY(cudaMemcpyAsync(d_host, d, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ED_CUDA_TRY(cudaMemcpyAsync(e_host, e, (size_t)(m - 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return ED_OK;
+}
+
+ed_status tridiag_blocked_setup(OzContext* oz, double* A, int m, const OzOperand& opA, const OzOperand& opB,
+                                const double* NVW, const double* WV, std::vector<OzSliceJob>& jobs,
+                                std::vector<OzProblem>& probs) {
+  for (const TriPanel& P : tridiag_panels(m)) {
+    const int mm = m - P.t0;
+    OzOperand a = opA, b = opB;
+    int ma = 0, mb = 0;
+    ED_TRY(oz_map(oz, &a, mm, kKw, true, &ma));
+    ED_TRY(oz_map(oz, &b, mm, kKw, false, &mb));
+    for (int side = 0; side < 2; ++side) {
+      OzSliceJob jb{};
+      jb.src = (side == 0 ? NVW : WV) + (long long)P.t0 * kKw;
+      jb.sbase = 0;
+      jb.ld = kKw;
+      jb.rows = mm;
+      jb.cols = kKw;
+      jb.dst = side == 0 ? a.slices : b.slices;
+      jb.exps = side == 0 ? a.exps : b.exps;
+      jb.Kpad = kKw;
+      jb.first = side == 0 ? 0 : mm;
+      jobs.push_back(jb);
+    }
+    OzProblem pr{};
+    pr.mapA = ma;
+    pr.mapB = mb;
+    pr.ea = a.exps;
+    pr.eb = b.exps;
+    pr.C = A + (long long)P.t0 * m + P.t0;
+    pr.cbase = 0;
+    pr.ldc = m;
+    pr.M = pr.N = mm;
+    pr.K = kKw;
+    pr.acc = 1;
+    pr.tiles_n = (mm + kOzBN - 1) / kOzBN;
+    pr.tri = 1;
+    pr.tile0 = 0;
+    probs.push_back(pr);
+  }
   return ED_OK;
 }
 

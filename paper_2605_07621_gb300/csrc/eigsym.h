@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "ed_internal.h"
+#include "ozaki.h"
 
 namespace edk {
 // Reduce the symmetric m x m row-major A (device; only its lower triangle,
@@ -14,6 +15,42 @@ namespace edk {
 // work: device scratch of tridiag_work_doubles(m) doubles.
 inline long long tridiag_work_doubles(int m) { return 8LL * m + 2LL * ((m + 31) / 32) * m; }
 ed_status tridiag_reduce(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st, int sms);
+// Blocked reduction: panels of kTriNb reflectors, each followed by the
+// trailing update A -= V W^T + W V^T as one FP64-accurate tensor-core product
+constexpr int kTriNb = 64;
+struct TriPanel {
+  int k0, jb, t0;  // first column, reflectors, first row of the trailing matrix
+};
+std::vector<TriPanel> tridiag_panels(int m);
+// the panel buffers (device [m][2 kTriNb] FP64 each), the float-float copy
+// of the matrix (device [m][ldF] float2, ldF = tridiag_ldF(m); every value
+// finite, since the reduction also reads entries outside the trailing
+// triangle, multiplied by zero), a 2-D tensor map over it (m x m 8-byte
+// elements, row stride ldF, box 34 x 32), the flag that bounded waits set,
+// and, per panel, two slicing jobs and one product (built by
+// tridiag_blocked_setup, on device)
+inline long long tridiag_ldF(int m) { return m + (m & 1); }
+struct TriBlocked {
+  OzContext* oz;
+  double* NVW;
+  double* WV;
+  float2* F;
+  long long ldF;
+  CUtensorMap tmF;
+  int* err;
+  const OzSliceJob* d_jobs;
+  const OzProblem* d_probs;
+};
+// appends the jobs and products of an m x m reduction of A (tensor maps in oz;
+// opA / opB: digit-plane buffers for m x 2 kTriNb operands)
+ed_status tridiag_blocked_setup(OzContext* oz, double* A, int m, const OzOperand& opA, const OzOperand& opB,
+                                const double* NVW, const double* WV, std::vector<OzSliceJob>& jobs,
+                                std::vector<OzProblem>& probs);
+inline long long tridiag_blocked_work_doubles(int m) {
+  return 6LL * m + 2LL * ((m + 63) / 64) * m + 128LL * (2 * kTriNb + 1) + 2 * kTriNb + 4096 + 1024 + 8;
+}
+ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st,
+                                 int sms, const TriBlocked& tb);
 // all eigenvalues of the tridiagonal (d, e) into d (unordered); false if the
 // iteration did not converge
 bool tridiag_eigenvalues(std::vector<double>& d, std::vector<double>& e);

@@ -86,7 +86,9 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
   DevMem mem;
   double *G = nullptr, *work = nullptr;
   ED_TRY(mem.get((void**)&G, (size_t)mmax * mmax * sizeof(double)));
-  ED_TRY(mem.get((void**)&work, (size_t)tridiag_work_doubles((int)mmax) * sizeof(double)));
+  ED_TRY(mem.get((void**)&work, (size_t)std::max(tridiag_work_doubles((int)mmax),
+                                                  tridiag_blocked_work_doubles((int)mmax)) *
+                                     sizeof(double)));
 
   // digit planes of one block at a time (both factors of its Gram matrix),
   // tensor maps and launch lists of every block built up front
@@ -137,7 +139,34 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     probs.push_back(p);
     tiles.push_back(oz_tiles(m, m, 1));
   }
+  // the blocked reduction's trailing updates: panel buffers, digit planes,
+  // and per block its panels' slicing jobs and products
+  double *NVW = nullptr, *WV = nullptr;
+  float2* F = nullptr;
+  OzOperand opA, opB;
+  ED_TRY(mem.get((void**)&F, (size_t)mmax * tridiag_ldF((int)mmax) * sizeof(float2)));
+  ED_CUDA_TRY(cudaMemsetAsync(F, 0, (size_t)mmax * tridiag_ldF((int)mmax) * sizeof(float2), st));
+  ED_TRY(oz_alloc(&oz, (void**)&NVW, (size_t)mmax * 2 * kTriNb * sizeof(double)));
+  ED_TRY(oz_alloc(&oz, (void**)&WV, (size_t)mmax * 2 * kTriNb * sizeof(double)));
+  ED_TRY(oz_operand_buffer(&oz, mmax * 2 * kTriNb, mmax, &opA));
+  ED_TRY(oz_operand_buffer(&oz, mmax * 2 * kTriNb, mmax, &opB));
+  std::vector<OzSliceJob> tjobs;
+  std::vector<OzProblem> tprobs;
+  std::vector<size_t> toff(c->blocks.size());
+  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+    const Block& b = c->blocks[bi];
+    toff[bi] = tprobs.size();
+    ED_TRY(tridiag_blocked_setup(&oz, G, (int)std::min(b.dA, b.dB), opA, opB, NVW, WV, tjobs, tprobs));
+  }
   ED_TRY(oz_finish(&oz));
+  OzSliceJob* d_tjobs = nullptr;
+  OzProblem* d_tprobs = nullptr;
+  if (!tprobs.empty()) {
+    ED_TRY(oz_alloc(&oz, (void**)&d_tjobs, tjobs.size() * sizeof(OzSliceJob)));
+    ED_TRY(oz_alloc(&oz, (void**)&d_tprobs, tprobs.size() * sizeof(OzProblem)));
+    ED_CUDA_TRY(cudaMemcpy(d_tjobs, tjobs.data(), tjobs.size() * sizeof(OzSliceJob), cudaMemcpyHostToDevice));
+    ED_CUDA_TRY(cudaMemcpy(d_tprobs, tprobs.data(), tprobs.size() * sizeof(OzProblem), cudaMemcpyHostToDevice));
+  }
   OzSliceJob* d_jobs = nullptr;
   OzProblem* d_probs = nullptr;
   ED_TRY(oz_alloc(&oz, (void**)&d_jobs, jobs.size() * sizeof(OzSliceJob)));
@@ -183,11 +212,14 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     ED_CUDA_TRY(cudaEventRecord(ev.e[1], st));
     dd[bi].assign(m, 0.0);
     ee[bi].assign(std::max(m - 1, 1), 0.0);
-    ED_TRY(tridiag_reduce(G, m, work, dd[bi].data(), ee[bi].data(), st, sms));
+    TriBlocked tb{&oz, NVW, WV, F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi], d_tprobs + toff[bi]};
+    if (m >= 3) ED_TRY(tmap_8b_2d(&tb.tmF, F, m, m, tb.ldF, 34, 32));
+    ED_TRY(tridiag_reduce_blocked(G, m, work, dd[bi].data(), ee[bi].data(), st, sms, tb));
     ED_CUDA_TRY(cudaEventRecord(ev.e[2], st));
     // ||Psi_s||^2 (the trace of rho_A(s)) with the library's FP64 reduction
     ED_TRY(dot_dev<double>(c, xb, xb, b.dA * b.dB, slot(c, 3), st, 0));
     ED_TRY(read_scalars(c, 3, 1, &wt[bi], st));  // synchronises the stream
+    ED_TRY(oz_status(&oz, st));                   // no bounded wait of the block's kernels ran out
     float t1 = 0.f, t2 = 0.f;
     ED_CUDA_TRY(cudaEventElapsedTime(&t1, ev.e[0], ev.e[1]));
     ED_CUDA_TRY(cudaEventElapsedTime(&t2, ev.e[1], ev.e[2]));

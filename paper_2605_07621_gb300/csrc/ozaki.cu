@@ -105,6 +105,41 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
+ed_status tmap_8b_2d(CUtensorMap* m, const void* base, long long cols, long long rows, long long ld, int box_cols,
+                     int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return ED_ECUDA;
+  }
+  cudaFree(nullptr);  // a current context for the driver call (see tmap_bf16_planes)
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld matrix", (int)r, rows, cols);
+    return ED_ECUDA;
+  }
+  return ED_OK;
+}
+
+ed_status oz_status(OzContext* o, cudaStream_t st) {
+  if (!o->d_err) return ED_OK;
+  int h = 0;
+  ED_CUDA_TRY(cudaMemcpyAsync(&h, o->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ED_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h != 0) {
+    ED_CUDA_TRY(cudaMemsetAsync(o->d_err, 0, sizeof(int), st));
+    set_error("a tensor-core kernel's wait for its operands ran out (code %d)", h);
+    return ED_ECUDA;
+  }
+  return ED_OK;
+}
+
 ed_status tmap_bf16_planes(CUtensorMap* m, const void* base, int K, int R, int planes, long long Kpad, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {

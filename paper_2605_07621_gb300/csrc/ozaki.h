@@ -67,6 +67,14 @@ ed_status oz_alloc(OzContext* o, void** p, size_t bytes);
 // Kpad elements, a multiple of 8; planes one after another), box
 // (64, box_rows, 1), 128-byte swizzle, elements outside the matrix read as 0
 ed_status tmap_bf16_planes(CUtensorMap* m, const void* base, int K, int R, int planes, long long Kpad, int box_rows);
+// 2-D tensor map over a rows x cols matrix of 8-byte elements (row stride ld
+// elements, ld * 8 a multiple of 16), box (box_cols, box_rows), no swizzle,
+// elements outside the matrix read as 0
+ed_status tmap_8b_2d(CUtensorMap* m, const void* base, long long cols, long long rows, long long ld, int box_cols,
+                     int box_rows);
+// reads and clears the flag that the tensor-core kernels set when one of
+// their bounded waits ran out (synchronises the stream); ED_ECUDA if set
+ed_status oz_status(OzContext* o, cudaStream_t st);
 // operand from a host FP64 row-major matrix (digits formed on the host)
 ed_status oz_operand_host(OzContext* o, const double* h, int R, int K, bool a_role, OzOperand* out);
 // operand buffers filled on the device by oz_slice_* (no data yet)
