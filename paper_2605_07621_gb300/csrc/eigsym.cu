@@ -18,11 +18,13 @@
 //     the fly (column c, and p = A v - V (W^T v) - W (V^T v)); after the
 //     panel the trailing matrix takes A -= V W^T + W V^T in one
 //     FP64-accurate tensor-core product (rank 2 kTriNb, lower-triangle
-//     tiles).  The product A v, the whole cost of the reduction, reads a
-//     float-float copy of the panel's starting matrix (48 significant bits,
-//     error-free products and sums on the FP32 pipe inside 64 x 64 units,
-//     FP64 across units): on this GPU FP64 arithmetic runs about 70 times
-//     slower than FP32, and the float-float pass is bound by HBM instead.
+//     tiles).  Within the panel every step -- the column, the product A v
+//     (the whole cost of the reduction), the pending terms and the dots --
+//     reads a float-float copy of the panel's starting matrix and runs in
+//     float-float arithmetic (48 significant bits, error-free products and
+//     sums on the FP32 pipe): on this GPU FP64 arithmetic runs about 70
+//     times slower than FP32, and the float-float product is bound by HBM
+//     instead.
 //     Per column three kernels: the column and its reflector (k_pcol), the
 //     product (k_symv), its sums and the pending terms (k_psum2).
 //  2. The eigenvalues of the tridiagonal matrix by implicit QL steps with
@@ -201,16 +203,21 @@ __global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e
   }
 }
 
-// ---- blocked reduction: panel kernels.  WV row r holds w_0..w_{nb-1} at
-// columns 0..nb-1 and v_0..v_{nb-1} at nb..2nb-1 (the panel's reflectors so
-// far, zero elsewhere); NVW holds the same with the halves swapped and
-// negated (the operands of the trailing update).  Within a panel the
-// products A v read a float-float copy F of the panel's starting matrix:
-// a = hi + lo with two FP32 values (48 significant bits), scaled by a power
-// of two 2^sh that brings the largest entry into [1/2, 1), so that the
-// products run on the FP32 pipe (this GPU's FP64 pipe is about 70 times
-// slower) with error-free products (FMA) and sums (Knuth's TwoSum) inside a
-// 64 x 64 unit, and every unit's sums meet in FP64.
+// ---- blocked reduction: panel kernels.  The panel's columns are reduced
+// against a float-float copy F of the panel's starting matrix: a = hi + lo
+// with two FP32 values (48 significant bits), the whole matrix scaled by a
+// power of two sigma = 2^sh that brings its largest entry into [1/2, 1).
+// All per-column work runs in float-float arithmetic on the FP32 pipe --
+// error-free products (FMA) and sums (Knuth's TwoSum) -- because this GPU's
+// FP64 pipe is about 70 times slower; scalars (norms, beta, K) are FP64.  The
+// reflectors take LAPACK's normalisation (dlarfg): v = x / (x_1 - alpha), so
+// v_1 = 1, |v_i| <= 1 and beta = (|alpha| + |x_1|) / |alpha| lies in [1, 2],
+// which keeps every float-float quantity within FP32's exponent range however
+// small the column; v is the same for sigma A and A, w scales with sigma.  So
+// the panel keeps sigma W (columns 0..nb-1) and V (columns nb..2nb-1) in WVf;
+// at the panel's end they become the FP64 operands of the trailing update,
+// WV = (W, V) and NVW = (-V, -W).  A column whose norm is below 2^-60 of the
+// scaled matrix (below FP64's resolution of it) is taken as already reduced.
 constexpr int kNb = kTriNb, kKw = 2 * kTriNb;
 constexpr int kU = 64;             // edge of the product's units
 constexpr int kSvWarps = 2;        // warps (units in flight) per CTA of the product
@@ -256,6 +263,9 @@ __device__ __forceinline__ float2 split_scaled(double a, int sh) {
   return make_float2(hi, __uint_as_float(s | ((unsigned)(el + 127) << 23) | frac));
 }
 
+// float-float value as FP64 (exact for a normalised pair)
+__device__ __forceinline__ double df_to_d(float2 a) { return (double)a.x + (double)a.y; }
+
 // (sh, sl) += (ah + al)(bh + bl): ah bh split exactly into p + e (FMA), p
 // added to sh by TwoSum, the rounding error, e and the cross terms into sl
 // (al bl, below 2^-48 of the product, is dropped).  The _rn intrinsics keep
@@ -268,6 +278,38 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
   const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
   sh = s;
   sl = __fadd_rn(sl, __fadd_rn(err, fmaf(ah, bl, fmaf(al, bh, e))));
+}
+__device__ __forceinline__ void df_fma(float2& s, float2 a, float2 b) { df_fma(s.x, s.y, a.x, a.y, b.x, b.y); }
+
+// (sh, sl) += (bh, bl) for two float-float sums (TwoSum of the leading parts)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+  const float s = __fadd_rn(sh, bh);
+  const float z = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(bh, z));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, bl));
+}
+__device__ __forceinline__ void df_add(float2& s, float2 b) { df_add(s.x, s.y, b.x, b.y); }
+// the pair renormalised (|lo| at most half an ulp of hi)
+__device__ __forceinline__ float2 df_norm(float2 a) {
+  const float s = __fadd_rn(a.x, a.y);
+  return make_float2(s, __fsub_rn(a.y, __fsub_rn(s, a.x)));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// a b as a normalised pair
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float2 s = make_float2(0.f, 0.f);
+  df_fma(s, a, b);
+  return df_norm(s);
+}
+// warp-wide float-float sum; lane 0's result is the one to use (the low
+// parts of the other lanes may differ in their last bits)
+__device__ __forceinline__ float2 df_warp_sum(float2 a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, a.x, o), bl = __shfl_xor_sync(0xffffffffu, a.y, o);
+    df_add(a.x, a.y, bh, bl);
+  }
+  return a;
 }
 
 __device__ inline unsigned long long warp_umax(unsigned long long x) {
@@ -304,9 +346,8 @@ __global__ void __launch_bounds__(256) k_amax(const double* __restrict__ A, int 
 }
 
 // the float-float copy F = split(A 2^sh) of the trailing triangle (row
-// stride ldF); sh (the
-// same in every CTA, written to *shp by CTA 0) brings the largest magnitude
-// into [1/2, 1)
+// stride ldF); sh (the same in every CTA, written to *shp by CTA 0) brings
+// the largest magnitude into [1/2, 1)
 __global__ void __launch_bounds__(256) k_pconv(const double* __restrict__ A, float2* __restrict__ F, long long ldF,
                                                int m, int r0, const unsigned long long* __restrict__ amx, int na,
                                                int* shp) {
@@ -331,35 +372,43 @@ __global__ void __launch_bounds__(256) k_pconv(const double* __restrict__ A, flo
   }
 }
 
-// column c of the matrix with the panel's pending updates, rows c+1..m-1,
-// into v (and its scaled split into vf); one warp per kPr rows at a time,
-// lanes over the panel's terms.  Column j - 1 of the panel (the previous
-// reflector) is not stored yet: its w' = beta' p - K' v' (from the previous
-// column's p, v, beta and K) is formed here, row by row, and stored with v'
-// as it is used.  Per CTA: the partial sums W^T x (slots 0..nb-1), V^T x
-// (slots nb..2nb-1) over rows c+1.. and the sum of squares below row c+1
-// (slot 2nb); the last CTA to finish (a ticket on *ctr) adds them up in a
-// fixed order and forms the reflector of column c: beta_c, d_c, e_c, v[c+1]
-// (and vf[c+1]) and, for j > 0, tu = (W^T v, V^T v), where v differs from x
-// only in row c+1 (v = x - alpha e_{c+1}).
-__global__ void __launch_bounds__(256) k_pcol(const double* __restrict__ A, int m, int c, int j,
-                                              double* __restrict__ WV, double* __restrict__ v,
-                                              float2* __restrict__ vf, const int* __restrict__ shp,
-                                              const double* __restrict__ p, double* beta, const double* Kp,
-                                              double* __restrict__ cp, unsigned* ctr, double* d, double* e,
-                                              double* __restrict__ tu) {
-  __shared__ double acc[8][kKw + 1];
-  __shared__ double tot[kKw + 1];
-  __shared__ double s_alpha, s_vw;
+// column c of the scaled matrix with the panel's pending updates, rows
+// c+1..m-1: x = F[., c] - V (sigma W)[c]^T - (sigma W) V[c]^T, into vf; one
+// warp per kPr rows at a time, lanes over the panel's terms.  Column j - 1
+// (the previous reflector) is not stored yet: its w' = beta' p - K' v' (from
+// the previous column's pf, vf, beta and K) is formed here row by row and
+// stored with v' as it is used.  Per CTA: the partial sums (sigma W)^T x
+// (slots 0..nb-1), V^T x (slots nb..2nb-1) over rows c+1.. and the sum of
+// squares below row c+1 (slot 2nb); the last CTA to finish (a ticket on
+// *ctr) adds them up in a fixed order and forms the reflector of column c:
+// beta_c (FP64 and float-float), d_c, e_c (unscaled), vf[c+1], the factor
+// tau (*tauf) with v = tau (x - alpha e_{c+1}) -- vf keeps x until k_psum2
+// has applied it -- and, for j > 0, tu = ((sigma W)^T v, V^T v).
+__global__ void __launch_bounds__(256) k_pcol(const float2* __restrict__ F, long long ldF, int m, int c, int j,
+                                              float2* __restrict__ WVf, float2* __restrict__ vf,
+                                              const float2* __restrict__ pf, double* beta, float2* betaf,
+                                              const float2* Kf, const int* __restrict__ shp, float2* __restrict__ cp,
+                                              unsigned* ctr, double* d, double* e, float2* __restrict__ tu,
+                                              float2* tauf) {
+  __shared__ float2 acc[8][kKw + 1];
+  __shared__ float2 tot[kKw + 1];
+  __shared__ float2 s_alpha, s_vw, s_tau;
   __shared__ unsigned s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sh = *shp;
+  const float2 z2 = make_float2(0.f, 0.f);
   const int jp = j - 1;  // the pending column formed here (none for j = 0)
-  const double bp = j > 0 ? beta[c - 1] : 0.0, Kq = j > 0 ? *Kp : 0.0;
-  const double vpc = j > 0 ? v[c] : 0.0, wpc = j > 0 ? bp * p[c] - Kq * vpc : 0.0;  // v'_c, w'_c
-  const double* rc = WV + (long long)c * kKw;
-  double w0 = lane < jp ? rc[lane] : 0.0, w1 = lane + 32 < jp ? rc[lane + 32] : 0.0;
-  double v0 = lane < jp ? rc[kNb + lane] : 0.0, v1 = lane + 32 < jp ? rc[kNb + lane + 32] : 0.0;
+  const float2 bq = j > 0 ? betaf[c - 1] : z2, kq = j > 0 ? *Kf : z2;
+  // w'_r = beta' p_r - K' v'_r
+  auto wprev = [&](float2 pr, float2 vr) {
+    float2 s = z2;
+    df_fma(s, bq, pr);
+    df_fma(s, df_neg(kq), vr);
+    return df_norm(s);
+  };
+  const float2 vpc = j > 0 ? vf[c] : z2, wpc = j > 0 ? wprev(pf[c], vpc) : z2;  // v'_c, w'_c
+  const float2* rc = WVf + (long long)c * kKw;
+  float2 w0 = lane < jp ? rc[lane] : z2, w1 = lane + 32 < jp ? rc[lane + 32] : z2;
+  float2 v0 = lane < jp ? rc[kNb + lane] : z2, v1 = lane + 32 < jp ? rc[kNb + lane + 32] : z2;
   if (lane == jp) {
     w0 = wpc;
     v0 = vpc;
@@ -369,25 +418,24 @@ __global__ void __launch_bounds__(256) k_pcol(const double* __restrict__ A, int 
     v1 = vpc;
   }
   if (j > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    WV[(long long)c * kKw + jp] = wpc;
-    WV[(long long)c * kKw + kNb + jp] = vpc;
+    WVf[(long long)c * kKw + jp] = wpc;
+    WVf[(long long)c * kKw + kNb + jp] = vpc;
   }
-  const long long ld = m;
-  double s2 = 0.0, dw0 = 0.0, dw1 = 0.0, dv0 = 0.0, dv1 = 0.0;
+  float2 s2 = z2, dw0 = z2, dw1 = z2, dv0 = z2, dv1 = z2;
   for (int rb = c + 1 + (blockIdx.x * 8 + warp) * kPr; rb < m; rb += gridDim.x * 8 * kPr) {
-    double a[kPr], t[kPr], rw0[kPr], rw1[kPr], rv0[kPr], rv1[kPr], wq[kPr], vq[kPr];
+    float2 a[kPr], t[kPr], rw0[kPr], rw1[kPr], rv0[kPr], rv1[kPr], wq[kPr], vq[kPr];
 #pragma unroll
     for (int q = 0; q < kPr; ++q) {
       const int r = rb + q;
       const bool in = r < m;
-      const double* row = WV + (long long)(in ? r : c) * kKw;
-      a[q] = in ? A[(long long)r * ld + c] : 0.0;
-      rw0[q] = in && lane < jp ? row[lane] : 0.0;
-      rv0[q] = in && lane < jp ? row[kNb + lane] : 0.0;
-      rw1[q] = in && lane + 32 < jp ? row[lane + 32] : 0.0;
-      rv1[q] = in && lane + 32 < jp ? row[kNb + lane + 32] : 0.0;
-      vq[q] = j > 0 && in ? v[r] : 0.0;  // v'_r, read before this kernel overwrites it
-      wq[q] = j > 0 && in ? bp * p[r] - Kq * vq[q] : 0.0;
+      const float2* row = WVf + (long long)(in ? r : c) * kKw;
+      a[q] = in ? F[(long long)r * ldF + c] : z2;
+      rw0[q] = in && lane < jp ? row[lane] : z2;
+      rv0[q] = in && lane < jp ? row[kNb + lane] : z2;
+      rw1[q] = in && lane + 32 < jp ? row[lane + 32] : z2;
+      rv1[q] = in && lane + 32 < jp ? row[kNb + lane + 32] : z2;
+      vq[q] = j > 0 && in ? vf[r] : z2;  // v'_r, read before this kernel overwrites it
+      wq[q] = j > 0 && in ? wprev(pf[r], vq[q]) : z2;
       if (lane == jp) {
         rw0[q] = wq[q];
         rv0[q] = vq[q];
@@ -396,32 +444,49 @@ __global__ void __launch_bounds__(256) k_pcol(const double* __restrict__ A, int 
         rw1[q] = wq[q];
         rv1[q] = vq[q];
       }
-      t[q] = rv0[q] * w0 + rw0[q] * v0 + rv1[q] * w1 + rw1[q] * v1;
+      float2 s = z2;
+      df_fma(s, rv0[q], w0);
+      df_fma(s, rw0[q], v0);
+      df_fma(s, rv1[q], w1);
+      df_fma(s, rw1[q], v1);
+      t[q] = s;
     }
     if (j > 0) {
       for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int q = 0; q < kPr; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+        for (int q = 0; q < kPr; ++q) {
+          const float bh = __shfl_xor_sync(0xffffffffu, t[q].x, o), bl = __shfl_xor_sync(0xffffffffu, t[q].y, o);
+          df_add(t[q].x, t[q].y, bh, bl);
+        }
+      }
+      // TwoSum's low part is not commutative, so the butterfly leaves the
+      // lanes with slightly different sums; x is a small difference of large
+      // terms and every lane must use the value stored in vf: lane 0's
+#pragma unroll
+      for (int q = 0; q < kPr; ++q) {
+        t[q].x = __shfl_sync(0xffffffffu, t[q].x, 0);
+        t[q].y = __shfl_sync(0xffffffffu, t[q].y, 0);
       }
     }
 #pragma unroll
     for (int q = 0; q < kPr; ++q) {
       const int r = rb + q;
       if (r >= m) break;
-      const double x = a[q] - t[q];
+      float2 x = a[q];
+      df_add(x, df_neg(t[q]));
+      x = df_norm(x);
       if (lane == 0) {
         if (j > 0) {
-          WV[(long long)r * kKw + jp] = wq[q];
-          WV[(long long)r * kKw + kNb + jp] = vq[q];
+          WVf[(long long)r * kKw + jp] = wq[q];
+          WVf[(long long)r * kKw + kNb + jp] = vq[q];
         }
-        v[r] = x;
-        vf[r] = split_scaled(x, sh);
-        if (r > c + 1) s2 += x * x;
+        vf[r] = x;
+        if (r > c + 1) df_fma(s2, x, x);
       }
-      dw0 += rw0[q] * x;
-      dv0 += rv0[q] * x;
-      dw1 += rw1[q] * x;
-      dv1 += rv1[q] * x;
+      df_fma(dw0, rw0[q], x);
+      df_fma(dv0, rv0[q], x);
+      df_fma(dw1, rw1[q], x);
+      df_fma(dv1, rv1[q], x);
     }
   }
   acc[warp][lane] = dw0;
@@ -431,8 +496,8 @@ __global__ void __launch_bounds__(256) k_pcol(const double* __restrict__ A, int 
   if (lane == 0) acc[warp][kKw] = s2;
   __syncthreads();
   for (int k = threadIdx.x; k <= kKw; k += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += acc[w][k];
+    float2 s = z2;
+    for (int w = 0; w < 8; ++w) df_add(s, acc[w][k]);
     cp[(long long)blockIdx.x * (kKw + 1) + k] = s;
   }
   __threadfence();
@@ -445,48 +510,62 @@ __global__ void __launch_bounds__(256) k_pcol(const double* __restrict__ A, int 
   // of every other CTA's partials, then the halves meet
   {
     const int k = threadIdx.x & (kKw - 1), hf = threadIdx.x >> 7;
-    double s = 0.0;
-#pragma unroll 16
-    for (int b = hf; b < (int)gridDim.x; b += 2) s += cp[(long long)b * (kKw + 1) + k];
+    float2 s = z2;
+#pragma unroll 8
+    for (int b = hf; b < (int)gridDim.x; b += 2) df_add(s, cp[(long long)b * (kKw + 1) + k]);
     acc[hf][k] = s;
     if (warp == 0) {  // slot 2 nb (the sum of squares)
-      double q = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) q += cp[(long long)b * (kKw + 1) + kKw];
-      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      float2 q = z2;
+      for (int b = lane; b < (int)gridDim.x; b += 32) df_add(q, cp[(long long)b * (kKw + 1) + kKw]);
+      q = df_warp_sum(q);
       if (lane == 0) tot[kKw] = q;
     }
   }
   __syncthreads();
-  if (threadIdx.x < kKw) tot[threadIdx.x] = acc[0][threadIdx.x] + acc[1][threadIdx.x];
-  if (warp == 0) {  // sum_i V[c,i] W[c,i] (the diagonal's pending update)
-    double t = 0.0;
-    if (lane < j) t += rc[kNb + lane] * rc[lane];
-    if (lane + 32 < j) t += rc[kNb + lane + 32] * rc[lane + 32];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (threadIdx.x < kKw) {
+    float2 s = acc[0][threadIdx.x];
+    df_add(s, acc[1][threadIdx.x]);
+    tot[threadIdx.x] = df_norm(s);
+  }
+  if (warp == 0) {  // sum_i V[c,i] (sigma W)[c,i] (the diagonal's pending update)
+    float2 t = z2;
+    if (lane < j) df_fma(t, rc[kNb + lane], rc[lane]);
+    if (lane + 32 < j) df_fma(t, rc[kNb + lane + 32], rc[lane + 32]);
+    t = df_warp_sum(t);
     if (lane == 0) s_vw = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     *ctr = 0u;
-    d[c] = A[(long long)c * ld + c] - 2.0 * s_vw;
-    const double tail = tot[kKw];
-    const double x0 = v[c + 1];
+    const int sh = *shp;
+    d[c] = ldexp(df_to_d(F[(long long)c * ldF + c]) - 2.0 * df_to_d(s_vw), -sh);
+    const double tail = df_to_d(tot[kKw]);
+    const double x0 = df_to_d(vf[c + 1]);
     const double nrm = sqrt(x0 * x0 + tail);
-    double alpha = 0.0;
-    if (tail == 0.0) {  // nothing to annihilate
-      e[c] = x0;
+    double alpha = 0.0, tau = 0.0;
+    if (tail == 0.0 || nrm < 0x1p-60) {  // nothing to annihilate
+      e[c] = ldexp(x0, -sh);
       beta[c] = 0.0;
+      betaf[c] = z2;
     } else {
       alpha = x0 >= 0.0 ? -nrm : nrm;
-      v[c + 1] = x0 - alpha;
-      vf[c + 1] = split_scaled(x0 - alpha, sh);
-      beta[c] = 1.0 / (nrm * (nrm + fabs(x0)));
-      e[c] = alpha;
+      tau = 1.0 / (x0 - alpha);  // v = tau x, v_{c+1} = tau (x0 - alpha)
+      vf[c + 1] = split_scaled(x0 - alpha, 0);
+      const double b = (nrm + fabs(x0)) / nrm;
+      beta[c] = b;
+      betaf[c] = split_scaled(b, 0);
+      e[c] = ldexp(alpha, -sh);
     }
-    s_alpha = alpha;
+    s_alpha = split_scaled(alpha, 0);
+    s_tau = split_scaled(tau, 0);
+    *tauf = s_tau;
   }
   __syncthreads();
-  if (j > 0 && threadIdx.x < kKw) tu[threadIdx.x] = tot[threadIdx.x] - s_alpha * WV[(long long)(c + 1) * kKw + threadIdx.x];
+  if (j > 0 && threadIdx.x < kKw && (threadIdx.x & (kNb - 1)) < j) {  // the slots of the panel's columns
+    float2 s = tot[threadIdx.x];
+    df_fma(s, df_neg(s_alpha), WVf[(long long)(c + 1) * kKw + threadIdx.x]);
+    tu[threadIdx.x] = df_mul(df_norm(s), s_tau);
+  }
 }
 
 // unit t of the triangle, numbered row by row: (I, J), J <= I
@@ -498,33 +577,25 @@ __device__ __forceinline__ void unit_ij(long long t, int& I, int& J) {
   J = (int)(t - i * (i + 1) / 2);
 }
 
-// (sh, sl) += (bh, bl) for two float-float sums (TwoSum of the leading parts)
-__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
-  const float s = __fadd_rn(sh, bh);
-  const float z = __fsub_rn(s, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(bh, z));
-  sh = s;
-  sl = __fadd_rn(sl, __fadd_rn(err, bl));
-}
-
 constexpr long long kSvSpin = 1LL << 24;  // polls of an mbarrier before k_symv gives up
 
-// partial sums of p = A v over the trailing triangle from the float-float
-// copy.  Units of 64 x 64 (I, J), J <= I, start at row and column u0 (r0
-// rounded down to even, so that every box starts on a 16-byte boundary; v is
-// zero below r0) and are numbered row by row; one warp per unit, as 2 x 2
-// sub-tiles of 32 x 32, each brought into shared memory by one TMA box of
-// 32 rows x 34 columns (the two extra columns give a 272-byte row pitch, free
-// of bank conflicts), two buffers per warp so that the next sub-tile (across
-// units) is in flight while one is summed.  Lane = column for the column sums
-// (a_ij v_i, kept in registers over the unit's rows), lane = row for the row
-// sums (a_ij v_j); two independent float-float chains each.  Diagonal
-// entries count once, for their row.  Unit (I, J) writes its row sums to slot
-// J and its column sums to slot TU + I of `part` (slot s, row i at
-// part[s * m + i]) in FP64; the sums are in units of 2^(2 sh).
+// partial sums of p = (sigma A) v over the trailing triangle from the
+// float-float copy (v = tau vf).  Units of 64 x 64 (I, J), J <= I, start at row and
+// column u0 (r0 rounded down to even, so that every box starts on a 16-byte
+// boundary; v is zero below r0) and are numbered row by row; one warp per
+// unit, as 2 x 2 sub-tiles of 32 x 32, each brought into shared memory by
+// one TMA box of 32 rows x 34 columns (the two extra columns give a 272-byte
+// row pitch, free of bank conflicts; F streams through L2 once per column,
+// marked evict-first), two buffers per warp so that the next sub-tile
+// (across units) is in flight while one is summed.  Lane = column for the
+// column sums (a_ij v_i, kept in registers over the unit's rows), lane = row
+// for the row sums (a_ij v_j); two independent float-float chains each.
+// Diagonal entries count once, for their row.  Unit (I, J) writes its row
+// sums to slot J and its column sums to slot TU + I of `part` (slot s, row i
+// at part[s * m + i]) as float-float pairs.
 __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ CUtensorMap tmF, int m, int r0,
-                                                        int u0, const float2* __restrict__ vf,
-                                                        double* __restrict__ part, int TU, long long nunits,
+                                                        int u0, const float2* __restrict__ vf, const float2* tauf,
+                                                        float2* __restrict__ part, int TU, long long nunits,
                                                         int* err) {
   __shared__ __align__(128) float2 tile[kSvWarps][2][32][kTs];
   __shared__ __align__(16) float2 vs[kSvWarps][2 * kU];  // the unit's row values, then its column values
@@ -547,7 +618,8 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
     unit_ij(t, I, J);
     return !(I == J && g < h) && u0 + I * kU + 32 * g < m;
   };
-  const uint64_t pol = tc::l2_evict_first();  // F streams through once per column; the small buffers stay in L2
+  const uint64_t pol = tc::l2_evict_first();
+  const float2 tau = *tauf;  // v = tau vf
   auto issue = [&](long long k) {
     int I, J;
     if (!present(k, I, J) || lane != 0) return;
@@ -575,8 +647,8 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
       __syncwarp();
       for (int q = lane; q < kU; q += 32) {
         const int a = ib + q, b = jb + q;
-        vs[w][q] = a >= r0 && a < m ? vf[a] : make_float2(0.f, 0.f);
-        vs[w][kU + q] = b >= r0 && b < m ? vf[b] : make_float2(0.f, 0.f);
+        vs[w][q] = a >= r0 && a < m ? df_mul(vf[a], tau) : make_float2(0.f, 0.f);
+        vs[w][kU + q] = b >= r0 && b < m ? df_mul(vf[b], tau) : make_float2(0.f, 0.f);
       }
       rh0 = rl0 = rh1 = rl1 = 0.f;
       __syncwarp();
@@ -635,135 +707,157 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
       else
         df_add(rh1, rl1, r2h, r2l);
     }
-    if (g == 1 && j >= r0 && j < m) part[(long long)(TU + I) * ld + j] = (double)ch + (double)cl;
+    if (g == 1 && j >= r0 && j < m) part[(long long)(TU + I) * ld + j] = make_float2(ch, cl);
     if (s == 3) {
-      if (ib + lane >= r0 && ib + lane < m) part[(long long)J * ld + ib + lane] = (double)rh0 + (double)rl0;
-      if (ib + 32 + lane < m) part[(long long)J * ld + ib + 32 + lane] = (double)rh1 + (double)rl1;
+      if (ib + lane >= r0 && ib + lane < m) part[(long long)J * ld + ib + lane] = make_float2(rh0, rl0);
+      if (ib + 32 + lane < m) part[(long long)J * ld + ib + 32 + lane] = make_float2(rh1, rl1);
     }
     __syncwarp();
     issue(k + 2);
   }
 }
 
-// p[i] for rows i >= r0: the unit slots that k_symv wrote (row slots 0..I(i),
-// column slots TU + I(i) .. TU + Tn - 1, units from u0), scaled back by
-// 2^(-2 sh), minus the panel's pending terms V (W^T v) + W (V^T v); kPsT
-// threads per row.  Per CTA: the partial sum of p.v; the last CTA to finish
-// (a ticket on *ctr) adds them in a fixed order into K = beta^2 p.v / 2 (*Kp),
-// which makes w = beta p - K v.
-__global__ void __launch_bounds__(256) k_psum2(const double* __restrict__ part, int m, int r0, int u0, int TU, int Tn,
-                                               const int* __restrict__ shp, const double* __restrict__ WV,
-                                               const double* __restrict__ tu, int j, const double* __restrict__ v,
-                                               double* __restrict__ p, double* __restrict__ pvp,
-                                               const double* beta, int c, unsigned* ctr, double* Kp) {
-  __shared__ double red[33];
+// p[i] for rows i >= r0 (pf, float-float, in the scaled matrix; vf[i] becomes
+// v = tau vf): the unit
+// slots that k_symv wrote (row slots 0..I(i), column slots TU + I(i) .. TU +
+// Tn - 1, units from u0), minus the panel's pending terms
+// V ((sigma W)^T v) + (sigma W) (V^T v); kPsT threads per row.  Per CTA: the
+// partial sum of p.v; the last CTA to finish (a ticket on *ctr) adds them in
+// a fixed order into K = beta^2 p.v / 2 (*Kp, FP64, and *Kf), which makes
+// w = beta p - K v.
+__global__ void __launch_bounds__(256) k_psum2(const float2* __restrict__ part, int m, int r0, int u0, int TU, int Tn,
+                                               const float2* __restrict__ WVf, const float2* __restrict__ tu, int j,
+                                               float2* __restrict__ vf, const float2* tauf, float2* __restrict__ pf,
+                                               float2* __restrict__ pvp, const double* beta, int c, unsigned* ctr,
+                                               float2* Kf) {
+  __shared__ float2 red[8];
   __shared__ unsigned s_last;
-  const int q = threadIdx.x & (kPsT - 1);
-  const int sh = *shp;
+  const int q = threadIdx.x & (kPsT - 1), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long ld = m;
-  double pv = 0.0;
+  const float2 z2 = make_float2(0.f, 0.f);
+  const float2 tau = *tauf;
+  float2 pv = z2;
   constexpr int rows_cta = 256 / kPsT;
   for (int base = r0 + blockIdx.x * rows_cta; base < m; base += gridDim.x * rows_cta) {
     const int i = base + threadIdx.x / kPsT;
-    double s = 0.0, corr = 0.0;
+    float2 s = z2, corr = z2;
     if (i < m) {
       const int Ii = (i - u0) / kU;
-#pragma unroll 8
-      for (int J = q; J <= Ii; J += kPsT) s += part[(long long)J * ld + i];
-#pragma unroll 8
-      for (int I = Ii + q; I < Tn; I += kPsT) s += part[(long long)(TU + I) * ld + i];
-      const double* row = WV + (long long)i * kKw;
 #pragma unroll 4
-      for (int k = q; k < j; k += kPsT) corr += row[kNb + k] * tu[k] + row[k] * tu[kNb + k];
+      for (int J = q; J <= Ii; J += kPsT) df_add(s, part[(long long)J * ld + i]);
+#pragma unroll 4
+      for (int I = Ii + q; I < Tn; I += kPsT) df_add(s, part[(long long)(TU + I) * ld + i]);
+      const float2* row = WVf + (long long)i * kKw;
+#pragma unroll 4
+      for (int k = q; k < j; k += kPsT) {
+        df_fma(corr, row[kNb + k], tu[k]);
+        df_fma(corr, row[k], tu[kNb + k]);
+      }
     }
+    df_add(s, df_neg(corr));
     for (int o = kPsT / 2; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      corr += __shfl_xor_sync(0xffffffffu, corr, o);
+      const float bh = __shfl_xor_sync(0xffffffffu, s.x, o), bl = __shfl_xor_sync(0xffffffffu, s.y, o);
+      df_add(s.x, s.y, bh, bl);
     }
     if (i < m && q == 0) {
-      const double pi = ldexp(ldexp(s, -sh), -sh) - corr;
-      p[i] = pi;
-      pv += pi * v[i];
+      const float2 pi = df_norm(s), vi = df_mul(vf[i], tau);
+      pf[i] = pi;
+      vf[i] = vi;  // v itself from here on
+      df_fma(pv, pi, vi);
     }
   }
-  pv = block_sum(pv, red);
-  if (threadIdx.x == 0) pvp[blockIdx.x] = pv;
+  pv = df_warp_sum(pv);
+  if (lane == 0) red[warp] = pv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 t = z2;
+    for (int w = 0; w < 8; ++w) df_add(t, red[w]);
+    pvp[blockIdx.x] = t;
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1 ? 1u : 0u;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += pvp[b];
-  s = block_sum(s, red);
+  float2 t = z2;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) df_add(t, pvp[b]);
+  t = df_warp_sum(t);
+  if (lane == 0) red[warp] = t;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    float2 u = z2;
+    for (int w = 0; w < 8; ++w) df_add(u, red[w]);
     const double b = beta[c];
-    *Kp = 0.5 * b * b * s;
+    *Kf = split_scaled(0.5 * b * b * df_to_d(u), 0);
     *ctr = 0u;
   }
 }
 
-// w = beta p - K v over rows c+1..m-1 (p = A v without beta), stored with v
-// as column j of the panel (the panel's last column; the others are stored
-// by the next column's k_pcol)
-__global__ void __launch_bounds__(256) k_pw(int m, int c, int j, const double* __restrict__ v,
-                                            const double* __restrict__ p, const double* Kp, const double* beta,
-                                            double* __restrict__ WV) {
-  const double b = beta[c], K = *Kp;
+// w = beta p - K v over rows c+1..m-1, stored with v as column j of the
+// panel (the panel's last column; the others are stored by the next
+// column's k_pcol)
+__global__ void __launch_bounds__(256) k_pw(int m, int c, int j, const float2* __restrict__ vf,
+                                            const float2* __restrict__ pf, const float2* Kf, const float2* betaf,
+                                            float2* __restrict__ WVf) {
+  const float2 b = betaf[c], K = df_neg(*Kf);
   for (int r = c + 1 + blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-    const double vr = v[r];
-    WV[(long long)r * kKw + j] = b * p[r] - K * vr;
-    WV[(long long)r * kKw + kNb + j] = vr;
+    const float2 vr = vf[r];
+    float2 s = make_float2(0.f, 0.f);
+    df_fma(s, b, pf[r]);
+    df_fma(s, K, vr);
+    WVf[(long long)r * kKw + j] = df_norm(s);
+    WVf[(long long)r * kKw + kNb + j] = vr;
   }
 }
 
-__device__ inline double block_max(double x, double* red) {
-  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+__device__ inline float block_maxf(float x, float* red) {
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) red[w] = x;
   __syncthreads();
   if (w == 0) {
-    x = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    x = l < (int)(blockDim.x >> 5) ? red[l] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
     if (l == 0) red[32] = x;
   }
   __syncthreads();
   return red[32];
 }
 
-// after the panel: column j of v scaled by 2^k and of w by 2^-k (their
-// product unchanged) so that their largest magnitudes meet, and the negated
-// swapped copy NVW; the trailing product slices each operand row with one
-// exponent across all the panel's v and w, and this keeps either half from
-// losing its low digits to the other.  One CTA per column.
-__global__ void __launch_bounds__(256) k_pbal(int m, int k0, double* __restrict__ WV, double* __restrict__ NVW) {
-  __shared__ double red[33];
+// after the panel: the FP64 operands of the trailing update from WVf, column
+// j of v scaled by 2^k and of w (sigma w unscaled) by 2^-k (their product
+// unchanged) so that their largest magnitudes meet, and the negated swapped
+// copy NVW; the trailing product slices each operand row with one exponent
+// across all the panel's v and w, and this keeps either half from losing its
+// low digits to the other.  One CTA per column.
+__global__ void __launch_bounds__(256) k_pbal(int m, int k0, const float2* __restrict__ WVf, const int* shp,
+                                              double* __restrict__ WV, double* __restrict__ NVW) {
+  __shared__ float red[33];
   const int j = blockIdx.x, c = k0 + j;
-  double mv = 0.0, mw = 0.0;
+  const int sh = *shp;
+  float mv = 0.f, mw = 0.f;
   for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
-    mv = fmax(mv, fabs(WV[(long long)r * kKw + kNb + j]));
-    mw = fmax(mw, fabs(WV[(long long)r * kKw + j]));
+    mv = fmaxf(mv, fabsf(WVf[(long long)r * kKw + kNb + j].x));
+    mw = fmaxf(mw, fabsf(WVf[(long long)r * kKw + j].x));
   }
-  mv = block_max(mv, red);
-  mw = block_max(mw, red);
+  mv = block_maxf(mv, red);
+  mw = block_maxf(mw, red);
   int k = 0;
-  if (mv > 0.0 && mw > 0.0) {
+  if (mv > 0.f && mw > 0.f) {
     int ev, ew;
-    frexp(mv, &ev);
-    frexp(mw, &ew);
-    k = (ew - ev) / 2;
+    frexpf(mv, &ev);
+    frexpf(mw, &ew);
+    k = ((ew - sh) - ev) / 2;  // w = (sigma w) 2^-sh
   }
-  const double sv = ldexp(1.0, k), sw = ldexp(1.0, -k);
   for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
-    double* row = WV + (long long)r * kKw;
-    double* nrow = NVW + (long long)r * kKw;
-    const double vi = row[kNb + j] * sv, wi = row[j] * sw;
-    row[kNb + j] = vi;
-    row[j] = wi;
-    nrow[j] = -vi;
-    nrow[kNb + j] = -wi;
+    const float2* row = WVf + (long long)r * kKw;
+    const double vi = ldexp(df_to_d(row[kNb + j]), k), wi = ldexp(df_to_d(row[j]), -sh - k);
+    WV[(long long)r * kKw + kNb + j] = vi;
+    WV[(long long)r * kKw + j] = wi;
+    NVW[(long long)r * kKw + j] = -vi;
+    NVW[(long long)r * kKw + kNb + j] = -wi;
   }
 }
 
@@ -829,55 +923,56 @@ std::vector<TriPanel> tridiag_panels(int m) {
 ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st,
                                  int sms, const TriBlocked& tb) {
   if (m < 3) return tridiag_reduce(A, m, work, d_host, e_host, st, sms);
-  const int TU = (m + kU - 1) / kU;
-  double* v = work;
-  double* p = work + m;
-  double* beta = work + 2 * m;
-  double* d = work + 3 * m;
-  double* e = work + 4 * m;
-  float2* vf = reinterpret_cast<float2*>(work + 5 * m);
-  double* part = work + 6 * m;                                   // 2 TU slots of m
-  double* cp = part + 2LL * TU * m;                              // k_pcol partials (kPcolCtas x (2 nb + 1))
-  double* tu = cp + (long long)kPcolCtas * (kKw + 1);            // W^T v, V^T v (2 nb)
-  double* pvp = tu + kKw;                                        // p.v partials (kRowCtas)
-  auto* amx = reinterpret_cast<unsigned long long*>(pvp + kRowCtas);  // kAmaxCtas
-  double* Kp = reinterpret_cast<double*>(amx + kAmaxCtas);       // K of the latest column
-  int* shp = reinterpret_cast<int*>(Kp + 1);                     // the panel's scale exponent
-  unsigned* ctr = reinterpret_cast<unsigned*>(Kp + 2);           // tickets of k_pcol and k_psum2
-  ED_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st));
   auto cdiv = [](long long a, long long b) { return (a + b - 1) / b; };
+  const int TU = (int)cdiv(m, kU);
+  float2* vf = reinterpret_cast<float2*>(work);          // sigma v of the latest column
+  float2* pf = reinterpret_cast<float2*>(work + m);      // its p (scaled)
+  double* beta = work + 2 * m;
+  float2* betaf = reinterpret_cast<float2*>(work + 3 * m);
+  double* d = work + 4 * m;
+  double* e = work + 5 * m;
+  float2* part = reinterpret_cast<float2*>(work + 6 * m);  // 2 TU slots of m
+  float2* cp = part + 2LL * TU * m;                         // k_pcol partials (kPcolCtas x (2 nb + 1))
+  float2* tu = cp + (long long)kPcolCtas * (kKw + 1);       // W^T v, (sigma V)^T v (2 nb)
+  float2* pvp = tu + kKw;                                   // p.v partials (kRowCtas)
+  auto* amx = reinterpret_cast<unsigned long long*>(pvp + kRowCtas);  // kAmaxCtas
+  float2* Kf = reinterpret_cast<float2*>(amx + kAmaxCtas);  // K of the latest column
+  int* shp = reinterpret_cast<int*>(Kf + 1);                // the panel's scale exponent
+  unsigned* ctr = reinterpret_cast<unsigned*>(Kf + 2);      // tickets of k_pcol and k_psum2
+  float2* tauf = Kf + 3;                                    // tau of the latest column
+  ED_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st));
   const std::vector<TriPanel> pan = tridiag_panels(m);
   for (size_t q = 0; q < pan.size(); ++q) {
     const TriPanel& P = pan[q];
     ED_CUDA_TRY(cudaMemsetAsync(tb.WV + (long long)P.k0 * kKw, 0, (size_t)(m - P.k0) * kKw * sizeof(double), st));
     ED_CUDA_TRY(cudaMemsetAsync(tb.NVW + (long long)P.k0 * kKw, 0, (size_t)(m - P.k0) * kKw * sizeof(double), st));
-    // float-float copy of the panel's trailing triangle (rows and columns >= k0 + 1)
+    // float-float copy of the panel's trailing triangle (rows and columns >= k0)
     {
-      const int r0 = P.k0 + 1;
-      const int ga = (int)std::max(1LL, std::min((long long)kAmaxCtas, cdiv(m - r0, 8)));
-      k_amax<<<ga, 256, 0, st>>>(A, m, r0, amx);
-      const int gc = (int)std::max(1LL, std::min((long long)sms * 8, cdiv(m - r0, 8)));
-      k_pconv<<<gc, 256, 0, st>>>(A, tb.F, tb.ldF, m, r0, amx, ga, shp);
+      const int ga = (int)std::max(1LL, std::min((long long)kAmaxCtas, cdiv(m - P.k0, 8)));
+      k_amax<<<ga, 256, 0, st>>>(A, m, P.k0, amx);
+      const int gc = (int)std::max(1LL, std::min((long long)sms * 8, cdiv(m - P.k0, 8)));
+      k_pconv<<<gc, 256, 0, st>>>(A, tb.F, tb.ldF, m, P.k0, amx, ga, shp);
     }
     for (int j = 0; j < P.jb; ++j) {
       const int c = P.k0 + j;
       const int n = m - c - 1;  // rows and columns of the product, from c + 1
       const int g1 = (int)std::max(1LL, std::min((long long)kPcolCtas, cdiv(n, 8 * kPr)));
-      k_pcol<<<g1, 256, 0, st>>>(A, m, c, j, tb.WV, v, vf, shp, p, beta, Kp, cp, ctr, d, e, tu);
+      k_pcol<<<g1, 256, 0, st>>>(tb.F, tb.ldF, m, c, j, tb.WVf, vf, pf, beta, betaf, Kf, shp, cp, ctr, d, e, tu,
+                                 tauf);
       const int u0 = (c + 1) & ~1;  // the units' origin: even, so that the boxes start 16-byte aligned
       const long long Tn = cdiv(m - u0, kU), nu = Tn * (Tn + 1) / 2;
       const int gs = (int)std::max(1LL, std::min((long long)sms * 6, cdiv(nu, kSvWarps)));
-      k_symv<<<gs, 32 * kSvWarps, 0, st>>>(tb.tmF, m, c + 1, u0, vf, part, TU, nu, tb.err);
+      k_symv<<<gs, 32 * kSvWarps, 0, st>>>(tb.tmF, m, c + 1, u0, vf, tauf, part, TU, nu, tb.err);
       const int g4 = (int)std::max(1LL, std::min((long long)kRowCtas, cdiv(n, 256 / kPsT)));
-      k_psum2<<<g4, 256, 0, st>>>(part, m, c + 1, u0, TU, (int)Tn, shp, tb.WV, tu, j, v, p, pvp, beta, c, ctr + 1,
-                                  Kp);
+      k_psum2<<<g4, 256, 0, st>>>(part, m, c + 1, u0, TU, (int)Tn, tb.WVf, tu, j, vf, tauf, pf, pvp, beta, c,
+                                  ctr + 1, Kf);
     }
     {
       const int c = P.k0 + P.jb - 1;
       const int g5 = (int)std::max(1LL, std::min((long long)sms * 2, cdiv(m - c - 1, 256)));
-      k_pw<<<g5, 256, 0, st>>>(m, c, P.jb - 1, v, p, Kp, beta, tb.WV);
+      k_pw<<<g5, 256, 0, st>>>(m, c, P.jb - 1, vf, pf, Kf, betaf, tb.WVf);
     }
-    k_pbal<<<P.jb, 256, 0, st>>>(m, P.k0, tb.WV, tb.NVW);
+    k_pbal<<<P.jb, 256, 0, st>>>(m, P.k0, tb.WVf, shp, tb.WV, tb.NVW);
     // trailing matrix (rows and columns >= t0): A -= V W^T + W V^T
     ED_TRY(oz_slice(tb.oz, tb.d_jobs + 2 * q, 2, 2LL * (m - P.t0), false, nullptr, st));
     ED_TRY(oz_gemm(tb.oz, tb.d_probs + q, 1, oz_tiles(m - P.t0, m - P.t0, 1), nullptr, st));

@@ -22,7 +22,7 @@ struct TriPanel {
   int k0, jb, t0;  // first column, reflectors, first row of the trailing matrix
 };
 std::vector<TriPanel> tridiag_panels(int m);
-// the panel buffers (device [m][2 kTriNb] FP64 each), the float-float copy
+// the panel buffers (device [m][2 kTriNb] FP64 each, and WVf), the float-float copy
 // of the matrix (device [m][ldF] float2, ldF = tridiag_ldF(m); every value
 // finite, since the reduction also reads entries outside the trailing
 // triangle, multiplied by zero), a 2-D tensor map over it (m x m 8-byte
@@ -34,6 +34,7 @@ struct TriBlocked {
   OzContext* oz;
   double* NVW;
   double* WV;
+  float2* WVf;  // the panel's W and sigma V as float-float pairs (device [m][2 kTriNb])
   float2* F;
   long long ldF;
   CUtensorMap tmF;

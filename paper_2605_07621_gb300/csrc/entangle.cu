@@ -142,8 +142,9 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
   // the blocked reduction's trailing updates: panel buffers, digit planes,
   // and per block its panels' slicing jobs and products
   double *NVW = nullptr, *WV = nullptr;
-  float2* F = nullptr;
+  float2 *F = nullptr, *WVf = nullptr;
   OzOperand opA, opB;
+  ED_TRY(mem.get((void**)&WVf, (size_t)mmax * 2 * kTriNb * sizeof(float2)));
   ED_TRY(mem.get((void**)&F, (size_t)mmax * tridiag_ldF((int)mmax) * sizeof(float2)));
   ED_CUDA_TRY(cudaMemsetAsync(F, 0, (size_t)mmax * tridiag_ldF((int)mmax) * sizeof(float2), st));
   ED_TRY(oz_alloc(&oz, (void**)&NVW, (size_t)mmax * 2 * kTriNb * sizeof(double)));
@@ -212,7 +213,7 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     ED_CUDA_TRY(cudaEventRecord(ev.e[1], st));
     dd[bi].assign(m, 0.0);
     ee[bi].assign(std::max(m - 1, 1), 0.0);
-    TriBlocked tb{&oz, NVW, WV, F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi], d_tprobs + toff[bi]};
+    TriBlocked tb{&oz, NVW, WV, WVf, F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi], d_tprobs + toff[bi]};
     if (m >= 3) ED_TRY(tmap_8b_2d(&tb.tmF, F, m, m, tb.ldF, 34, 32));
     ED_TRY(tridiag_reduce_blocked(G, m, work, dd[bi].data(), ee[bi].data(), st, sms, tb));
     ED_CUDA_TRY(cudaEventRecord(ev.e[2], st));
