@@ -220,7 +220,9 @@ __global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e
 // scaled matrix (below FP64's resolution of it) is taken as already reduced.
 constexpr int kNb = kTriNb, kKw = 2 * kTriNb;
 constexpr int kU = 64;             // edge of the product's units
-constexpr int kSvWarps = 2;        // warps (units in flight) per CTA of the product
+constexpr int kSvWarps = 1;        // warps (units in flight) per CTA of the product
+constexpr int kSvBuf = 3;          // staging buffers (sub-tiles in flight) per warp
+constexpr int kSvCtas = 8;         // resident CTAs of the product per SM (shared memory)
 constexpr int kTs = 34;            // row stride (float2) of its staging tiles: 16-byte aligned rows
 constexpr int kPcolCtas = 128;     // most CTAs of k_pcol (partial-sum slots)
 constexpr int kRowCtas = 4096;     // most CTAs of k_psum2 (partial-sum slots)
@@ -586,8 +588,9 @@ constexpr long long kSvSpin = 1LL << 24;  // polls of an mbarrier before k_symv 
 // unit, as 2 x 2 sub-tiles of 32 x 32, each brought into shared memory by
 // one TMA box of 32 rows x 34 columns (the two extra columns give a 272-byte
 // row pitch, free of bank conflicts; F streams through L2 once per column,
-// marked evict-first), two buffers per warp so that the next sub-tile
-// (across units) is in flight while one is summed.  Lane = column for the
+// marked evict-first), kSvBuf buffers per warp so that the next sub-tiles
+// (across units) are in flight while one is summed, and the next unit's v
+// values are fetched a unit ahead.  Lane = column for the
 // column sums (a_ij v_i, kept in registers over the unit's rows), lane = row
 // for the row sums (a_ij v_j); two independent float-float chains each.
 // Diagonal entries count once, for their row.  Unit (I, J) writes its row
@@ -597,20 +600,20 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
                                                         int u0, const float2* __restrict__ vf, const float2* tauf,
                                                         float2* __restrict__ part, int TU, long long nunits,
                                                         int* err) {
-  __shared__ __align__(128) float2 tile[kSvWarps][2][32][kTs];
+  __shared__ __align__(128) float2 tile[kSvWarps][kSvBuf][32][kTs];
   __shared__ __align__(16) float2 vs[kSvWarps][2 * kU];  // the unit's row values, then its column values
-  __shared__ __align__(8) uint64_t bar[kSvWarps][2];
+  __shared__ __align__(8) uint64_t bar[kSvWarps][kSvBuf];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long ld = m;
   const long long t0 = (long long)blockIdx.x * kSvWarps + w, nw = (long long)gridDim.x * kSvWarps;
   if (lane == 0) {
-    tc::mbar_init(&bar[w][0], 1);
-    tc::mbar_init(&bar[w][1], 1);
+    for (int b = 0; b < kSvBuf; ++b) tc::mbar_init(&bar[w][b], 1);
     tc::fence_mbar_init();
   }
   __syncwarp();
   // sub-tile k of this warp: unit t0 + (k / 4) nw, s = k % 4 -> column half
-  // h = s / 2, row half g = s % 2; false if it holds nothing to sum
+  // h = s / 2, row half g = s % 2, buffer k % kSvBuf; false if it holds
+  // nothing to sum
   auto present = [&](long long k, int& I, int& J) {
     const long long t = t0 + (k >> 2) * nw;
     if (t >= nunits) return false;
@@ -620,22 +623,35 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
   };
   const uint64_t pol = tc::l2_evict_first();
   const float2 tau = *tauf;  // v = tau vf
-  auto issue = [&](long long k) {
+  auto issue = [&](long long k, int buf) {
     int I, J;
     if (!present(k, I, J) || lane != 0) return;
     const int s = (int)(k & 3), h = s >> 1, g = s & 1;
-    uint64_t* b = &bar[w][k & 1];
+    uint64_t* b = &bar[w][buf];
     tc::mbar_expect_tx(b, 32 * kTs * (unsigned)sizeof(float2));
-    tc::tma_load_2d_hint(tile[w][k & 1], &tmF, u0 + J * kU + 32 * h, u0 + I * kU + 32 * g, b, pol);
+    tc::tma_load_2d_hint(tile[w][buf], &tmF, u0 + J * kU + 32 * h, u0 + I * kU + 32 * g, b, pol);
   };
-  issue(0);
-  issue(1);
+  for (int b = 0; b < kSvBuf; ++b) issue(b, b);
+  // the v values of a unit (rows ib + lane, ib + 32 + lane, columns likewise),
+  // fetched one unit ahead
+  const float2 z2 = make_float2(0.f, 0.f);
+  auto fetch_v = [&](long long t, float2* nv) {
+    int I2, J2;
+    unit_ij(t, I2, J2);
+    const int a = u0 + I2 * kU + lane, c2 = u0 + J2 * kU + lane;
+    nv[0] = a >= r0 && a < m ? vf[a] : z2;
+    nv[1] = a + 32 >= r0 && a + 32 < m ? vf[a + 32] : z2;
+    nv[2] = c2 >= r0 && c2 < m ? vf[c2] : z2;
+    nv[3] = c2 + 32 >= r0 && c2 + 32 < m ? vf[c2 + 32] : z2;
+  };
+  float2 nv[4] = {z2, z2, z2, z2};
+  if (t0 < nunits) fetch_v(t0, nv);
   unsigned phases = 0u;  // bit b: parity of the next phase of buffer b
-  int I = 0, J = 0, ib = 0, jb = 0;
+  int I = 0, J = 0, ib = 0, jb = 0, bk = 0;
   bool diag = false;
   float rh0 = 0.f, rl0 = 0.f, rh1 = 0.f, rl1 = 0.f;  // row sums of rows ib + lane, ib + 32 + lane
   float ch = 0.f, cl = 0.f;                          // column sums of column jb + 32 h + lane
-  for (long long k = 0;; ++k) {
+  for (long long k = 0;; ++k, bk = bk + 1 == kSvBuf ? 0 : bk + 1) {
     const long long t = t0 + (k >> 2) * nw;
     if (t >= nunits) break;
     const int s = (int)(k & 3), h = s >> 1, g = s & 1;
@@ -645,11 +661,11 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
       ib = u0 + I * kU;
       jb = u0 + J * kU;
       __syncwarp();
-      for (int q = lane; q < kU; q += 32) {
-        const int a = ib + q, b = jb + q;
-        vs[w][q] = a >= r0 && a < m ? df_mul(vf[a], tau) : make_float2(0.f, 0.f);
-        vs[w][kU + q] = b >= r0 && b < m ? df_mul(vf[b], tau) : make_float2(0.f, 0.f);
-      }
+      vs[w][lane] = df_mul(nv[0], tau);
+      vs[w][lane + 32] = df_mul(nv[1], tau);
+      vs[w][kU + lane] = df_mul(nv[2], tau);
+      vs[w][kU + lane + 32] = df_mul(nv[3], tau);
+      if (t + nw < nunits) fetch_v(t + nw, nv);
       rh0 = rl0 = rh1 = rl1 = 0.f;
       __syncwarp();
     }
@@ -657,15 +673,18 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
     const int j = jb + 32 * h + lane;
     int Ik, Jk;
     if (present(k, Ik, Jk)) {
-      if (!tc::mbar_wait(&bar[w][k & 1], (phases >> (k & 1)) & 1u, kSvSpin)) {
-        // give up: record it, let the other buffer's copy land, stop
+      if (!tc::mbar_wait(&bar[w][bk], (phases >> bk) & 1u, kSvSpin)) {
+        // give up: record it, let the other buffers' copies land, stop
         if (lane == 0) atomicExch(err, 3);
-        int I2, J2;
-        if (present(k + 1, I2, J2)) tc::mbar_wait(&bar[w][(k + 1) & 1], (phases >> ((k + 1) & 1)) & 1u, kSvSpin);
+        for (int i = 1; i < kSvBuf; ++i) {
+          int I2, J2;
+          const int b2 = (bk + i) % kSvBuf;
+          if (present(k + i, I2, J2)) tc::mbar_wait(&bar[w][b2], (phases >> b2) & 1u, kSvSpin);
+        }
         return;
       }
-      phases ^= 1u << (k & 1);
-      const float2(*buf)[kTs] = tile[w][k & 1];
+      phases ^= 1u << bk;
+      const float2(*buf)[kTs] = tile[w][bk];
       const float2* xr = &vs[w][32 * g];
       const float2* xc = &vs[w][kU + 32 * h];
       float c2h = 0.f, c2l = 0.f, r2h = 0.f, r2l = 0.f, r3h = 0.f, r3l = 0.f;
@@ -713,7 +732,7 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
       if (ib + 32 + lane < m) part[(long long)J * ld + ib + 32 + lane] = make_float2(rh1, rl1);
     }
     __syncwarp();
-    issue(k + 2);
+    issue(k + kSvBuf, bk);
   }
 }
 
@@ -961,7 +980,7 @@ ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host,
                                  tauf);
       const int u0 = (c + 1) & ~1;  // the units' origin: even, so that the boxes start 16-byte aligned
       const long long Tn = cdiv(m - u0, kU), nu = Tn * (Tn + 1) / 2;
-      const int gs = (int)std::max(1LL, std::min((long long)sms * 6, cdiv(nu, kSvWarps)));
+      const int gs = (int)std::max(1LL, std::min((long long)sms * kSvCtas, cdiv(nu, kSvWarps)));
       k_symv<<<gs, 32 * kSvWarps, 0, st>>>(tb.tmF, m, c + 1, u0, vf, tauf, part, TU, nu, tb.err);
       const int g4 = (int)std::max(1LL, std::min((long long)kRowCtas, cdiv(n, 256 / kPsT)));
       k_psum2<<<g4, 256, 0, st>>>(part, m, c + 1, u0, TU, (int)Tn, tb.WVf, tu, j, vf, tauf, pf, pvp, beta, c,

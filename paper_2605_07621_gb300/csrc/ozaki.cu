@@ -517,6 +517,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         T[j] = h + l;
       }
     };
+    // an accumulating product reads its C tile after the products: bring the
+    // tile's rows into L2 now, while the tensor cores run
+    if (P.acc && rv) {
+#pragma unroll
+      for (int q = 0; q < kOzBN * 8 / 128; ++q) {
+        const int col = n0 + q * 16;
+        if (col < P.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + col));
+      }
+    }
     auto wait_chunk = [&](int c) -> bool {
       bool ok = false;
       for (long long it = 0; it < kOzSpin && !ok; ++it) {
