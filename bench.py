@@ -142,6 +142,20 @@ def entanglement_section(ed, ctx):
     xi_low = [float(-np.log(l[0] / tot)) if len(l) and l[0] > 0 else None for l in es.lam]
     peak, src = bf16_peak()
     achieved = tflops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None
+    # the reduction's dominant traffic: every column's product reads the
+    # float-float trailing triangle (8 bytes an entry) once; over the whole
+    # stage (every kernel of it in the time) this is a lower bound of the
+    # product kernel's rate
+    f_bytes = 0.0
+    for mb in m:
+        n = np.arange(int(mb) - 3, -1, -1, dtype=np.float64) + 2.0 if mb >= 3 else np.zeros(0)  # n = m - c - 1
+        f_bytes += float(np.sum(n * (n + 1) / 2)) * 8.0
+    peaks, psrc = measured_peaks()
+    stream_gbs = f_bytes / (eig_ms * 1e-3) / 1e9 if eig_ms > 0 else None
+    eig_stream = {"bytes": f_bytes, "achieved": stream_gbs, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                  "frac": stream_gbs / peaks["hbm_gbs"] if stream_gbs else None, "peak_source": psrc,
+                  "note": "float-float triangle bytes the per-column products read, over the whole eigenvalue "
+                          "stage's device time (panel kernels and trailing updates included)"}
     return {"ground_state_s": t_gs, "e0": r.e0, "seconds": t_es, "gram_ms": gram_ms, "eigensolver_ms": eig_ms,
             "gram_fp64_equiv_tflops": 2 * macs / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else None,
             "gram_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -149,6 +163,7 @@ def entanglement_section(ed, ctx):
                               "peak_source": f"{src} BF16 (burst)",
                               "note": "BF16 FLOPs executed by the digit-split products (36 digit pairs, padded "
                                       "tiles, the tiles on or below the diagonal)"},
+            "eigensolver_stream": eig_stream,
             "entropy": es.entropy, "s": [int(v) for v in s], "W_q": [float(v) for v in W],
             "xi_lowest_per_sector": xi_low, "n_eff_weights": float(1.0 / np.sum(W ** 2)),
             "n_eff_dims": float(1.0 / np.sum(w_dim ** 2)), "levels": int(sum(len(l) for l in es.lam))}
