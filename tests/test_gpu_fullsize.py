@@ -12,6 +12,8 @@ exact invariants of the method.
   oracle's stored coefficients (``make_golden.py hub12_gf_start``), so any
   difference comes from the Green's-function driver, not from the ground
   state.
+* The entanglement spectrum of the J1-J2 4x8 ground state: spin-flip partner
+  blocks carry the same spectrum, and the levels form a density matrix.
 """
 import json
 import os
@@ -147,3 +149,32 @@ def test_hub12_green_function_same_input_as_oracle(ed, oracle_mod):
         mg = _moments(w, a[:300], b[:299], c, r, 80)
         mo = _moments(g["w_" + side], ao, bo, c, r, 80)
         assert np.abs(mg - mo).max() <= 1e-10, (side, np.abs(mg - mo).max())
+
+
+def test_j1j2_4x8_entanglement_spin_flip(ed):
+    """Entanglement spectrum of the J1-J2 4x8 ground state (17 blocks, the
+    largest 12,870 x 12,870, every block reduced on its own).  The Sz = 0
+    ground state is an eigenvector of the global spin flip, which maps the
+    block with k up spins on A to the block with 16 - k and keeps its
+    singular values: the spectra of blocks k and 16 - k must agree (1e-12,
+    the oracle-parity tolerance of the spectra).  rho_A is a density matrix:
+    its levels sum to 1 and none is below -1e-12."""
+    import torch
+
+    ctx = ed.build_local_ops(ed.build_sectors(W.config_j1j2_4x8()))
+    psi = torch.empty(ctx.dim, dtype=torch.float64, device="cuda")
+    ed.lanczos_ground(ctx, mode="mixed", tol=1e-12, psi0=psi)
+    psi /= psi.norm()
+    es = ed.entanglement_spectrum(ctx, psi)
+    ctx.close()
+    del psi
+    torch.cuda.empty_cache()
+    assert list(es.s) == list(range(17))
+    for k in range(17):
+        a, b = es.lam[k], es.lam[16 - k]
+        assert a.shape == b.shape
+        assert np.max(np.abs(a - b)) <= 1e-12, (k, np.max(np.abs(a - b)))
+    levels = np.concatenate(es.lam)
+    assert levels.size == 2 ** 16
+    assert abs(levels.sum() - 1.0) <= 1e-12
+    assert levels.min() >= -1e-12
