@@ -322,6 +322,14 @@ __device__ inline unsigned long long warp_umax(unsigned long long x) {
   return x;
 }
 
+// programmatic dependent launch: let the stream's next kernel be scheduled
+// now (its CTAs wait in pdl_enter), then wait until the previous kernel has
+// finished and its writes are visible.  Called before any global access.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // largest |A[r][c]| over the trailing triangle r0 <= c <= r < m, per CTA, as
 // FP64 bit patterns without the sign (their unsigned order is the order of
 // the magnitudes); one warp per row
@@ -353,6 +361,7 @@ __global__ void __launch_bounds__(256) k_amax(const double* __restrict__ A, int 
 __global__ void __launch_bounds__(256) k_pconv(const double* __restrict__ A, float2* __restrict__ F, long long ldF,
                                                int m, int r0, const unsigned long long* __restrict__ amx, int na,
                                                int* shp) {
+  pdl_enter();
   __shared__ int s_sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(256) k_pcol(const float2* __restrict__ F, long
                                               const float2* Kf, const int* __restrict__ shp, float2* __restrict__ cp,
                                               unsigned* ctr, double* d, double* e, float2* __restrict__ tu,
                                               float2* tauf) {
+  pdl_enter();
   __shared__ float2 acc[8][kKw + 1];
   __shared__ float2 tot[kKw + 1];
   __shared__ float2 s_alpha, s_vw, s_tau;
@@ -611,6 +621,7 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
     tc::fence_mbar_init();
   }
   __syncwarp();
+  pdl_enter();
   // sub-tile k of this warp: unit t0 + (k / 4) nw, s = k % 4 -> column half
   // h = s / 2, row half g = s % 2, buffer k % kSvBuf; false if it holds
   // nothing to sum
@@ -749,6 +760,7 @@ __global__ void __launch_bounds__(256) k_psum2(const float2* __restrict__ part, 
                                                float2* __restrict__ vf, const float2* tauf, float2* __restrict__ pf,
                                                float2* __restrict__ pvp, const double* beta, int c, unsigned* ctr,
                                                float2* Kf) {
+  pdl_enter();
   __shared__ float2 red[8];
   __shared__ unsigned s_last;
   const int q = threadIdx.x & (kPsT - 1), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -819,6 +831,7 @@ __global__ void __launch_bounds__(256) k_psum2(const float2* __restrict__ part, 
 __global__ void __launch_bounds__(256) k_pw(int m, int c, int j, const float2* __restrict__ vf,
                                             const float2* __restrict__ pf, const float2* Kf, const float2* betaf,
                                             float2* __restrict__ WVf) {
+  pdl_enter();
   const float2 b = betaf[c], K = df_neg(*Kf);
   for (int r = c + 1 + blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
     const float2 vr = vf[r];
@@ -853,6 +866,7 @@ __device__ inline float block_maxf(float x, float* red) {
 // low digits to the other.  One CTA per column.
 __global__ void __launch_bounds__(256) k_pbal(int m, int k0, const float2* __restrict__ WVf, const int* shp,
                                               double* __restrict__ WV, double* __restrict__ NVW) {
+  pdl_enter();
   __shared__ float red[33];
   const int j = blockIdx.x, c = k0 + j;
   const int sh = *shp;
@@ -939,6 +953,24 @@ std::vector<TriPanel> tridiag_panels(int m) {
   return out;
 }
 
+// launch with programmatic stream serialization: the kernel may be
+// scheduled while the stream's previous kernel runs (each blocked-reduction
+// kernel starts with pdl_enter)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st,
                                  int sms, const TriBlocked& tb) {
   if (m < 3) return tridiag_reduce(A, m, work, d_host, e_host, st, sms);
@@ -970,28 +1002,28 @@ ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host,
       const int ga = (int)std::max(1LL, std::min((long long)kAmaxCtas, cdiv(m - P.k0, 8)));
       k_amax<<<ga, 256, 0, st>>>(A, m, P.k0, amx);
       const int gc = (int)std::max(1LL, std::min((long long)sms * 8, cdiv(m - P.k0, 8)));
-      k_pconv<<<gc, 256, 0, st>>>(A, tb.F, tb.ldF, m, P.k0, amx, ga, shp);
+      ED_CUDA_TRY(launch_pdl(k_pconv, gc, 256, st, A, tb.F, tb.ldF, m, P.k0, amx, ga, shp));
     }
     for (int j = 0; j < P.jb; ++j) {
       const int c = P.k0 + j;
       const int n = m - c - 1;  // rows and columns of the product, from c + 1
       const int g1 = (int)std::max(1LL, std::min((long long)kPcolCtas, cdiv(n, 8 * kPr)));
-      k_pcol<<<g1, 256, 0, st>>>(tb.F, tb.ldF, m, c, j, tb.WVf, vf, pf, beta, betaf, Kf, shp, cp, ctr, d, e, tu,
-                                 tauf);
+      ED_CUDA_TRY(launch_pdl(k_pcol, g1, 256, st, tb.F, tb.ldF, m, c, j, tb.WVf, vf, pf, beta, betaf, Kf, shp, cp, ctr,
+                             d, e, tu, tauf));
       const int u0 = (c + 1) & ~1;  // the units' origin: even, so that the boxes start 16-byte aligned
       const long long Tn = cdiv(m - u0, kU), nu = Tn * (Tn + 1) / 2;
       const int gs = (int)std::max(1LL, std::min((long long)sms * kSvCtas, cdiv(nu, kSvWarps)));
-      k_symv<<<gs, 32 * kSvWarps, 0, st>>>(tb.tmF, m, c + 1, u0, vf, tauf, part, TU, nu, tb.err);
+      ED_CUDA_TRY(launch_pdl(k_symv, gs, 32 * kSvWarps, st, tb.tmF, m, c + 1, u0, vf, tauf, part, TU, nu, tb.err));
       const int g4 = (int)std::max(1LL, std::min((long long)kRowCtas, cdiv(n, 256 / kPsT)));
-      k_psum2<<<g4, 256, 0, st>>>(part, m, c + 1, u0, TU, (int)Tn, tb.WVf, tu, j, vf, tauf, pf, pvp, beta, c,
-                                  ctr + 1, Kf);
+      ED_CUDA_TRY(launch_pdl(k_psum2, g4, 256, st, part, m, c + 1, u0, TU, (int)Tn, tb.WVf, tu, j, vf, tauf, pf, pvp,
+                             beta, c, ctr + 1, Kf));
     }
     {
       const int c = P.k0 + P.jb - 1;
       const int g5 = (int)std::max(1LL, std::min((long long)sms * 2, cdiv(m - c - 1, 256)));
-      k_pw<<<g5, 256, 0, st>>>(m, c, P.jb - 1, vf, pf, Kf, betaf, tb.WVf);
+      ED_CUDA_TRY(launch_pdl(k_pw, g5, 256, st, m, c, P.jb - 1, vf, pf, Kf, betaf, tb.WVf));
     }
-    k_pbal<<<P.jb, 256, 0, st>>>(m, P.k0, tb.WVf, shp, tb.WV, tb.NVW);
+    ED_CUDA_TRY(launch_pdl(k_pbal, P.jb, 256, st, m, P.k0, tb.WVf, shp, tb.WV, tb.NVW));
     // trailing matrix (rows and columns >= t0): A -= V W^T + W V^T
     ED_TRY(oz_slice(tb.oz, tb.d_jobs + 2 * q, 2, 2LL * (m - P.t0), false, nullptr, st));
     ED_TRY(oz_gemm(tb.oz, tb.d_probs + q, 1, oz_tiles(m - P.t0, m - P.t0, 1), nullptr, st));
@@ -1053,6 +1085,14 @@ ed_status tridiag_blocked_setup(OzContext* oz, double* A, int m, const OzOperand
 // numerically favoured form.  e[i] couples i and i+1; d is overwritten with
 // the eigenvalues (unordered), each within a few eps of the matrix norm.
 // false if a block needs more than 60 steps.
+// sqrt(a^2 + b^2); std::hypot's overflow and underflow guard only where the
+// squares could leave the FP64 range (it costs several times a square root)
+static inline double qhypot(double a, double b) {
+  const double m = std::max(std::fabs(a), std::fabs(b));
+  if (m > 0x1p+500 || (m < 0x1p-500 && m > 0.0)) return std::hypot(a, b);
+  return std::sqrt(a * a + b * b);
+}
+
 bool tridiag_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
   const int n = (int)d.size();
   if (n <= 1) return true;
@@ -1075,13 +1115,13 @@ bool tridiag_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
       if (iter == 60) return false;
       // shift: the eigenvalue of the leading 2 x 2 nearer d[l]
       double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = std::hypot(g, 1.0);
+      double r = qhypot(g, 1.0);
       g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
       double s = 1.0, c = 1.0, p = 0.0;
       bool split = false;
       for (int i = m - 1; i >= l; --i) {
         const double f = s * e[i], b = c * e[i];
-        r = std::hypot(f, g);
+        r = qhypot(f, g);
         e[i + 1] = r;
         if (r == 0.0) {  // the rotation vanished: the block splits at i + 1
           d[i + 1] -= p;
@@ -1089,8 +1129,9 @@ bool tridiag_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
           split = true;
           break;
         }
-        s = f / r;
-        c = g / r;
+        const double ri = 1.0 / r;
+        s = f * ri;
+        c = g * ri;
         g = d[i + 1] - p;
         r = (d[i] - g) * s + 2.0 * c * b;
         p = s * r;

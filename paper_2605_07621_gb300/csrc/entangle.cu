@@ -8,12 +8,16 @@
 // smaller of its two dimensions (the squared singular values of Psi_s).
 // The Gram matrix is formed on the tensor cores by the FP64-accurate
 // digit-split GEMM (ozaki.cu; one digit-plane buffer serves as both
-// factors, only the tiles on or below the diagonal), reduced to tridiagonal form on the GPU by Householder
-// reflections, and its eigenvalues come from implicit-shift QL on the host,
-// one thread per block while the GPU reduces the next block (eigsym.cu).
+// factors, only the tiles on or below the diagonal), reduced to tridiagonal
+// form on the GPU by Householder reflections (eigsym.cu), and its eigenvalues
+// come from implicit-shift QL on the host, one thread per block as soon as
+// its tridiagonal matrix is ready.  Blocks run concurrently on a few streams.
 #include <cmath>
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <string>
 #include <thread>
 
 #include "krylov.h"
@@ -37,14 +41,6 @@ struct DevMem {
     }
     p.push_back(*out);
     return ED_OK;
-  }
-};
-
-struct Events {
-  cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
-  ~Events() {
-    for (cudaEvent_t x : e)
-      if (x) cudaEventDestroy(x);
   }
 };
 
@@ -83,159 +79,317 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
   ED_DEVICE_SCOPE(c->device);
   ED_TRY(ensure_scratch(c));
   cudaStream_t st = (cudaStream_t)stream;
-  DevMem mem;
-  double *G = nullptr, *work = nullptr;
-  ED_TRY(mem.get((void**)&G, (size_t)mmax * mmax * sizeof(double)));
-  ED_TRY(mem.get((void**)&work, (size_t)std::max(tridiag_work_doubles((int)mmax),
-                                                  tridiag_blocked_work_doubles((int)mmax)) *
-                                     sizeof(double)));
+  const size_t nb = c->blocks.size();
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 148;
+  }
 
-  // digit planes of one block at a time (both factors of its Gram matrix),
-  // tensor maps and launch lists of every block built up front
+  // The blocks are reduced concurrently on up to kLanes streams ("lanes"):
+  // a column's kernels are short and leave most of the GPU idle on all but
+  // the largest blocks, so other blocks' columns fill it.  The largest block
+  // goes first and alone (its host QL is the longest and overlaps everything
+  // after it); the others go, largest first, to the lane with the least work
+  // so far (cost ~ m^3 / 3 for the products plus a fixed cost per column);
+  // each lane has its own buffers, sized for its largest block.
+  constexpr int kLanes = 3;
+  std::vector<size_t> order(nb);
+  for (size_t i = 0; i < nb; ++i) order[i] = i;
+  auto bm = [&](size_t i) { return (long long)std::min(c->blocks[i].dA, c->blocks[i].dB); };
+  auto bl = [&](size_t i) { return (long long)std::max(c->blocks[i].dA, c->blocks[i].dB); };
+  std::stable_sort(order.begin(), order.end(), [&](size_t u, size_t v) { return bm(u) > bm(v); });
+  // device bytes of a lane sized for blocks up to (m, m x Lpad elements)
+  auto lane_bytes = [&](long long m, long long xel) {
+    const long long ldF = tridiag_ldF((int)m);
+    return (double)m * m * 8 + (double)m * ldF * 8 + 3.0 * m * 2 * kTriNb * 8 +
+           8.0 * std::max(tridiag_work_doubles((int)m), tridiag_blocked_work_doubles((int)m)) +
+           2.0 * kOzDigits * xel + 2.0 * 2 * kOzDigits * m * 2 * kTriNb + 4.0 * m;
+  };
+  int lanes = kLanes;
+  {
+    size_t fr = 0, tot_mem = 0;
+    if (cudaMemGetInfo(&fr, &tot_mem) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    long long m0 = nb ? bm(order[0]) : 1, x0 = 1;
+    for (size_t i = 0; i < nb; ++i) x0 = std::max(x0, bm(i) * ((bl(i) + 7) / 8 * 8));
+    const double one = lane_bytes(m0, x0);
+    while (lanes > 1 && one * lanes > 0.8 * (double)fr) --lanes;
+  }
+  std::vector<int> lane_of(nb, 0);
+  std::vector<std::vector<size_t>> lane_blocks(lanes);
+  {
+    // the largest block first, alone (lane 0; the other lanes start when it
+    // is done), so that its host QL, the longest, overlaps all the rest
+    std::vector<double> load(lanes, 0.0);
+    if (nb) lane_blocks[0].push_back(order[0]);
+    for (size_t oi = 1; oi < nb; ++oi) {
+      const size_t bi = order[oi];
+      const double m = (double)bm(bi);
+      const double cost = m * m * m / 3.0 + 4e7 * m;
+      const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lane_of[bi] = k;
+      load[k] += cost;
+      lane_blocks[k].push_back(bi);
+    }
+  }
+  while (lanes > 1 && lane_blocks[lanes - 1].empty()) --lanes;
+
+  DevMem mem;
   OzContext oz;
   oz.device = c->device;
-  OzOperand X;
-  long long max_elems = 1;
-  for (const Block& b : c->blocks) {
-    const long long m = std::min(b.dA, b.dB), L = std::max(b.dA, b.dB);
-    max_elems = std::max(max_elems, m * ((L + 7) / 8 * 8));
+  struct Lane {
+    long long mmax = 1, xel = 1;
+    double *G = nullptr, *work = nullptr, *NVW = nullptr, *WV = nullptr;
+    float2 *F = nullptr, *WVf = nullptr;
+    OzOperand X, opA, opB;
+    cudaStream_t s = nullptr;
+  };
+  std::vector<Lane> L(lanes);
+  for (int k = 0; k < lanes; ++k) {
+    for (size_t bi : lane_blocks[k]) {
+      L[k].mmax = std::max(L[k].mmax, bm(bi));
+      L[k].xel = std::max(L[k].xel, bm(bi) * ((bl(bi) + 7) / 8 * 8));
+    }
+    const long long mk = L[k].mmax;
+    ED_TRY(mem.get((void**)&L[k].G, (size_t)mk * mk * sizeof(double)));
+    ED_TRY(mem.get((void**)&L[k].work, (size_t)std::max(tridiag_work_doubles((int)mk),
+                                                        tridiag_blocked_work_doubles((int)mk)) *
+                                           sizeof(double)));
+    ED_TRY(mem.get((void**)&L[k].F, (size_t)mk * tridiag_ldF((int)mk) * sizeof(float2)));
+    ED_TRY(mem.get((void**)&L[k].WVf, (size_t)mk * 2 * kTriNb * sizeof(float2)));
+    ED_TRY(oz_alloc(&oz, (void**)&L[k].NVW, (size_t)mk * 2 * kTriNb * sizeof(double)));
+    ED_TRY(oz_alloc(&oz, (void**)&L[k].WV, (size_t)mk * 2 * kTriNb * sizeof(double)));
+    ED_TRY(oz_operand_buffer(&oz, L[k].xel, mk, &L[k].X));
+    ED_TRY(oz_operand_buffer(&oz, mk * 2 * kTriNb, mk, &L[k].opA));
+    ED_TRY(oz_operand_buffer(&oz, mk * 2 * kTriNb, mk, &L[k].opB));
   }
-  ED_TRY(oz_operand_buffer(&oz, max_elems, mmax, &X));
-  std::vector<OzSliceJob> jobs;
-  std::vector<OzProblem> probs;
-  std::vector<long long> units, tiles;
-  for (const Block& b : c->blocks) {
-    const int m = (int)std::min(b.dA, b.dB), L = (int)std::max(b.dA, b.dB);
+
+  // per block: its Gram matrix (digit planes of Psi_s as both factors, the
+  // tiles on or below the diagonal) and the trailing updates of its
+  // reduction, in its lane's buffers; tensor maps and launch lists up front
+  std::vector<OzSliceJob> jobs(nb);
+  std::vector<OzProblem> probs(nb);
+  std::vector<long long> units(nb), tiles(nb);
+  std::vector<OzSliceJob> tjobs;
+  std::vector<OzProblem> tprobs;
+  std::vector<size_t> toff(nb);
+  for (size_t bi = 0; bi < nb; ++bi) {
+    const Block& b = c->blocks[bi];
+    Lane& ln = L[lane_of[bi]];
+    const int m = (int)bm(bi), Lg = (int)bl(bi);
     int ma = 0, mb = 0;
-    ED_TRY(oz_map(&oz, &X, m, L, true, &ma));
-    ED_TRY(oz_map(&oz, &X, m, L, false, &mb));
+    ED_TRY(oz_map(&oz, &ln.X, m, Lg, true, &ma));
+    ED_TRY(oz_map(&oz, &ln.X, m, Lg, false, &mb));
     OzSliceJob j{};
     j.src = psi + b.off;
     j.sbase = 0;
     j.ld = b.dB;
     j.rows = (int)b.dA;
     j.cols = (int)b.dB;
-    j.dst = X.slices;
-    j.exps = X.exps;
-    j.Kpad = (L + 7) / 8 * 8;
+    j.dst = ln.X.slices;
+    j.exps = ln.X.exps;
+    j.Kpad = (Lg + 7) / 8 * 8;
     j.first = 0;
-    jobs.push_back(j);
+    jobs[bi] = j;
     // Psi Psi^T (rows, dA <= dB) or Psi^T Psi (columns)
-    units.push_back(b.dA <= b.dB ? (long long)b.dA : (b.dB + 31) / 32);
+    units[bi] = b.dA <= b.dB ? (long long)b.dA : (b.dB + 31) / 32;
     OzProblem p{};
     p.mapA = ma;
     p.mapB = mb;
-    p.ea = X.exps;
-    p.eb = X.exps;
-    p.C = G;
+    p.ea = ln.X.exps;
+    p.eb = ln.X.exps;
+    p.C = ln.G;
     p.cbase = 0;
     p.ldc = m;
     p.M = p.N = m;
-    p.K = L;
+    p.K = Lg;
     p.acc = 0;
     p.tiles_n = (m + kOzBN - 1) / kOzBN;
     p.tri = 1;  // the lower triangle: all the reduction reads
     p.tile0 = 0;
-    probs.push_back(p);
-    tiles.push_back(oz_tiles(m, m, 1));
-  }
-  // the blocked reduction's trailing updates: panel buffers, digit planes,
-  // and per block its panels' slicing jobs and products
-  double *NVW = nullptr, *WV = nullptr;
-  float2 *F = nullptr, *WVf = nullptr;
-  OzOperand opA, opB;
-  ED_TRY(mem.get((void**)&WVf, (size_t)mmax * 2 * kTriNb * sizeof(float2)));
-  ED_TRY(mem.get((void**)&F, (size_t)mmax * tridiag_ldF((int)mmax) * sizeof(float2)));
-  ED_CUDA_TRY(cudaMemsetAsync(F, 0, (size_t)mmax * tridiag_ldF((int)mmax) * sizeof(float2), st));
-  ED_TRY(oz_alloc(&oz, (void**)&NVW, (size_t)mmax * 2 * kTriNb * sizeof(double)));
-  ED_TRY(oz_alloc(&oz, (void**)&WV, (size_t)mmax * 2 * kTriNb * sizeof(double)));
-  ED_TRY(oz_operand_buffer(&oz, mmax * 2 * kTriNb, mmax, &opA));
-  ED_TRY(oz_operand_buffer(&oz, mmax * 2 * kTriNb, mmax, &opB));
-  std::vector<OzSliceJob> tjobs;
-  std::vector<OzProblem> tprobs;
-  std::vector<size_t> toff(c->blocks.size());
-  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
-    const Block& b = c->blocks[bi];
+    probs[bi] = p;
+    tiles[bi] = oz_tiles(m, m, 1);
     toff[bi] = tprobs.size();
-    ED_TRY(tridiag_blocked_setup(&oz, G, (int)std::min(b.dA, b.dB), opA, opB, NVW, WV, tjobs, tprobs));
+    ED_TRY(tridiag_blocked_setup(&oz, ln.G, m, ln.opA, ln.opB, ln.NVW, ln.WV, tjobs, tprobs));
   }
   ED_TRY(oz_finish(&oz));
-  OzSliceJob* d_tjobs = nullptr;
-  OzProblem* d_tprobs = nullptr;
+  OzSliceJob *d_tjobs = nullptr, *d_jobs = nullptr;
+  OzProblem *d_tprobs = nullptr, *d_probs = nullptr;
   if (!tprobs.empty()) {
     ED_TRY(oz_alloc(&oz, (void**)&d_tjobs, tjobs.size() * sizeof(OzSliceJob)));
     ED_TRY(oz_alloc(&oz, (void**)&d_tprobs, tprobs.size() * sizeof(OzProblem)));
     ED_CUDA_TRY(cudaMemcpy(d_tjobs, tjobs.data(), tjobs.size() * sizeof(OzSliceJob), cudaMemcpyHostToDevice));
     ED_CUDA_TRY(cudaMemcpy(d_tprobs, tprobs.data(), tprobs.size() * sizeof(OzProblem), cudaMemcpyHostToDevice));
   }
-  OzSliceJob* d_jobs = nullptr;
-  OzProblem* d_probs = nullptr;
-  ED_TRY(oz_alloc(&oz, (void**)&d_jobs, jobs.size() * sizeof(OzSliceJob)));
-  ED_TRY(oz_alloc(&oz, (void**)&d_probs, probs.size() * sizeof(OzProblem)));
-  ED_CUDA_TRY(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(OzSliceJob), cudaMemcpyHostToDevice));
-  ED_CUDA_TRY(cudaMemcpy(d_probs, probs.data(), probs.size() * sizeof(OzProblem), cudaMemcpyHostToDevice));
+  ED_TRY(oz_alloc(&oz, (void**)&d_jobs, nb * sizeof(OzSliceJob)));
+  ED_TRY(oz_alloc(&oz, (void**)&d_probs, nb * sizeof(OzProblem)));
+  ED_CUDA_TRY(cudaMemcpy(d_jobs, jobs.data(), nb * sizeof(OzSliceJob), cudaMemcpyHostToDevice));
+  ED_CUDA_TRY(cudaMemcpy(d_probs, probs.data(), nb * sizeof(OzProblem), cudaMemcpyHostToDevice));
 
-  std::vector<double> wt(c->blocks.size());
-  // per block: its tridiagonal matrix, handed to a host thread for the QL
-  // steps while the GPU forms and reduces the next block
-  std::vector<std::vector<double>> dd(c->blocks.size()), ee(c->blocks.size());
-  std::vector<char> ok(c->blocks.size(), 1);
-  std::vector<std::thread> qr;
+  // pinned host arrays for every block's tridiagonal matrix
+  std::vector<size_t> hoff(nb + 1, 0);
+  for (size_t bi = 0; bi < nb; ++bi) hoff[bi + 1] = hoff[bi] + 2 * (size_t)std::max(bm(bi), 1LL);
+  struct Pinned {
+    double* p = nullptr;
+    ~Pinned() {
+      if (p) cudaFreeHost(p);
+    }
+  } hde;
+  ED_CUDA_TRY(cudaHostAlloc((void**)&hde.p, std::max<size_t>(hoff[nb], 1) * sizeof(double), cudaHostAllocDefault));
+  struct EventSet {
+    std::vector<cudaEvent_t> e;
+    ~EventSet() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+    ed_status make(size_t n) {
+      e.assign(n, nullptr);
+      for (cudaEvent_t& x : e) ED_CUDA_TRY(cudaEventCreate(&x));
+      return ED_OK;
+    }
+  } ev_g0, ev_g1, ev_done, ev_lane, ev_se;
+  ED_TRY(ev_g0.make(nb));
+  ED_TRY(ev_g1.make(nb));
+  ED_TRY(ev_done.make(nb));
+  ED_TRY(ev_lane.make(lanes));
+  ED_TRY(ev_se.make(3));
+  struct Streams {
+    std::vector<cudaStream_t> s;
+    ~Streams() {
+      for (cudaStream_t x : s) cudaStreamDestroy(x);
+    }
+  } own;
+  ED_CUDA_TRY(cudaEventRecord(ev_se.e[0], st));
+  for (int k = 0; k < lanes; ++k) {
+    cudaStream_t s = nullptr;
+    ED_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    own.s.push_back(s);
+    L[k].s = s;
+    ED_CUDA_TRY(cudaStreamWaitEvent(s, ev_se.e[0], 0));  // after the caller's work on its stream
+  }
+  // the reduction reads entries of F outside the trailing triangle (times
+  // zero): every value must be finite
+  for (int k = 0; k < lanes; ++k)
+    ED_CUDA_TRY(cudaMemsetAsync(L[k].F, 0, (size_t)L[k].mmax * tridiag_ldF((int)L[k].mmax) * sizeof(float2), L[k].s));
+
+  // per lane one host thread enqueues its blocks; per block one host thread
+  // waits for its tridiagonal matrix and runs the QL steps
+  std::vector<std::vector<double>> dd(nb), ee(nb);
+  std::vector<char> ok(nb, 1);
+  std::vector<std::thread> qr[kLanes];
+  std::vector<std::thread> workers;
   struct Joiner {
     std::vector<std::thread>* t;
+    int n;
     ~Joiner() {
-      for (auto& x : *t)
-        if (x.joinable()) x.join();
+      for (int i = 0; i < n; ++i)
+        for (auto& x : t[i])
+          if (x.joinable()) x.join();
     }
-  } joiner{&qr};
-  Events ev;
-  for (cudaEvent_t& x : ev.e) ED_CUDA_TRY(cudaEventCreate(&x));
-  double t_gram = 0.0, t_red = 0.0;
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
-    cudaGetLastError();
-    sms = 148;
+  };
+  Joiner jq{qr, kLanes};
+  Joiner jw{&workers, 1};
+  std::vector<ed_status> lst(lanes, ED_OK);
+  std::vector<std::string> lmsg(lanes);
+  // lane 0 records first_done after the largest block; the other lanes'
+  // streams wait for it (the host threads wait until it is recorded)
+  std::mutex fm;
+  std::condition_variable fcv;
+  int first_state = 0;  // 0: not yet, 1: recorded, 2: lane 0 failed before it
+  auto first_set = [&](int v) {
+    {
+      std::lock_guard<std::mutex> lk(fm);
+      first_state = v;
+    }
+    fcv.notify_all();
+  };
+  for (int k = 0; k < lanes; ++k) {
+    workers.emplace_back([&, k] {
+      auto fail = [&](ed_status s) {
+        lst[k] = s;
+        lmsg[k] = ed_last_error();
+        if (k == 0) first_set(2);
+      };
+      DeviceGuard dg(c->device);
+      if (dg.status() != ED_OK) return fail(ED_ECUDA);
+      Lane& ln = L[k];
+      if (k > 0) {
+        std::unique_lock<std::mutex> lk(fm);
+        fcv.wait(lk, [&] { return first_state != 0; });
+        if (first_state == 2) return;
+        lk.unlock();
+        if (cudaStreamWaitEvent(ln.s, ev_se.e[2], 0) != cudaSuccess) return fail(ED_ECUDA);
+      }
+      for (size_t bi : lane_blocks[k]) {
+        const Block& b = c->blocks[bi];
+        const int m = (int)bm(bi);
+        double* hd = hde.p + hoff[bi];
+        double* he = hd + std::max(m, 1);
+        ed_status s = ED_OK;
+        if (cudaEventRecord(ev_g0.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+        if ((s = oz_slice(&oz, d_jobs + bi, 1, units[bi], b.dA > b.dB, nullptr, ln.s)) != ED_OK) return fail(s);
+        if ((s = oz_gemm(&oz, d_probs + bi, 1, tiles[bi], nullptr, ln.s)) != ED_OK) return fail(s);
+        if (cudaEventRecord(ev_g1.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+        TriBlocked tb{&oz, ln.NVW, ln.WV, ln.WVf, ln.F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi],
+                      d_tprobs + toff[bi]};
+        if (m >= 3 && (s = tmap_8b_2d(&tb.tmF, ln.F, m, m, tb.ldF, 34, 32)) != ED_OK) return fail(s);
+        if ((s = tridiag_reduce_blocked(ln.G, m, ln.work, hd, he, ln.s, sms, tb)) != ED_OK) return fail(s);
+        if (cudaEventRecord(ev_done.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+        if (k == 0 && bi == lane_blocks[0][0]) {
+          if (cudaEventRecord(ev_se.e[2], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+          first_set(1);
+        }
+        cudaEvent_t done = ev_done.e[bi];
+        qr[k].emplace_back([&dd, &ee, &ok, hd, he, m, bi, done] {
+          if (cudaEventSynchronize(done) != cudaSuccess) {
+            ok[bi] = 2;
+            return;
+          }
+          dd[bi].assign(hd, hd + m);
+          ee[bi].assign(he, he + std::max(m - 1, 0));
+          ok[bi] = tridiag_eigenvalues(dd[bi], ee[bi]) ? 1 : 0;
+        });
+      }
+      if (cudaEventRecord(ev_lane.e[k], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+    });
   }
-  // largest blocks first: their host QL runs while the GPU handles the rest
-  std::vector<size_t> order(c->blocks.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](size_t u, size_t v) {
-    return std::min(c->blocks[u].dA, c->blocks[u].dB) > std::min(c->blocks[v].dA, c->blocks[v].dB);
-  });
-  for (size_t bi : order) {
+  for (auto& x : workers) x.join();
+  for (int k = 0; k < lanes; ++k)
+    if (lst[k] != ED_OK) {
+      for (int i = 0; i < lanes; ++i) cudaStreamSynchronize(L[i].s);  // nothing of this call left in flight
+      set_error("%s", lmsg[k].c_str());
+      return lst[k];
+    }
+  for (int k = 0; k < lanes; ++k) ED_CUDA_TRY(cudaStreamWaitEvent(st, ev_lane.e[k], 0));
+  ED_CUDA_TRY(cudaEventRecord(ev_se.e[1], st));
+  // ||Psi_s||^2 (the trace of rho_A(s)) with the library's FP64 reduction
+  std::vector<double> wt(nb);
+  for (size_t bi = 0; bi < nb; ++bi) {
     const Block& b = c->blocks[bi];
-    const double* xb = psi + b.off;
-    const int m = (int)std::min(b.dA, b.dB);
-    // Gram matrix in the smaller dimension: Psi Psi^T (rows) or Psi^T Psi (columns)
-    ED_CUDA_TRY(cudaEventRecord(ev.e[0], st));
-    ED_TRY(oz_slice(&oz, d_jobs + bi, 1, units[bi], b.dA > b.dB, nullptr, st));
-    ED_TRY(oz_gemm(&oz, d_probs + bi, 1, tiles[bi], nullptr, st));
-    ED_CUDA_TRY(cudaEventRecord(ev.e[1], st));
-    dd[bi].assign(m, 0.0);
-    ee[bi].assign(std::max(m - 1, 1), 0.0);
-    TriBlocked tb{&oz, NVW, WV, WVf, F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi], d_tprobs + toff[bi]};
-    if (m >= 3) ED_TRY(tmap_8b_2d(&tb.tmF, F, m, m, tb.ldF, 34, 32));
-    ED_TRY(tridiag_reduce_blocked(G, m, work, dd[bi].data(), ee[bi].data(), st, sms, tb));
-    ED_CUDA_TRY(cudaEventRecord(ev.e[2], st));
-    // ||Psi_s||^2 (the trace of rho_A(s)) with the library's FP64 reduction
-    ED_TRY(dot_dev<double>(c, xb, xb, b.dA * b.dB, slot(c, 3), st, 0));
+    ED_TRY(dot_dev<double>(c, psi + b.off, psi + b.off, b.dA * b.dB, slot(c, 3), st, 0));
     ED_TRY(read_scalars(c, 3, 1, &wt[bi], st));  // synchronises the stream
-    ED_TRY(oz_status(&oz, st));                   // no bounded wait of the block's kernels ran out
-    float t1 = 0.f, t2 = 0.f;
-    ED_CUDA_TRY(cudaEventElapsedTime(&t1, ev.e[0], ev.e[1]));
-    ED_CUDA_TRY(cudaEventElapsedTime(&t2, ev.e[1], ev.e[2]));
-    t_gram += t1;
-    t_red += t2;
-    ee[bi].resize(std::max(m - 1, 0));
-    qr.emplace_back([&dd, &ee, &ok, bi] { ok[bi] = tridiag_eigenvalues(dd[bi], ee[bi]) ? 1 : 0; });
   }
+  ED_TRY(oz_status(&oz, st));  // no bounded wait of the reduction's kernels ran out
   const auto tq = std::chrono::steady_clock::now();
-  for (auto& x : qr) x.join();
+  for (int k = 0; k < lanes; ++k)
+    for (auto& x : qr[k]) x.join();
   const double t_qr = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tq).count();
+  double t_gram = 0.0;
+  float t_all = 0.f;
+  for (size_t bi = 0; bi < nb; ++bi) {
+    float t1 = 0.f;
+    ED_CUDA_TRY(cudaEventElapsedTime(&t1, ev_g0.e[bi], ev_g1.e[bi]));
+    t_gram += t1;
+  }
+  ED_CUDA_TRY(cudaEventElapsedTime(&t_all, ev_se.e[0], ev_se.e[1]));
   int64_t pos = 0;
-  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
-    if (!ok[bi]) {
-      set_error("tridiagonal QL did not converge on block %zu", bi);
+  for (size_t bi = 0; bi < nb; ++bi) {
+    if (ok[bi] != 1) {
+      set_error(ok[bi] == 2 ? "waiting for block %zu's reduction failed" : "tridiagonal QL did not converge on block %zu",
+                bi);
       return ED_ENOCONV;
     }
     std::vector<double>& w = dd[bi];
@@ -244,8 +398,11 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     pos += (int64_t)w.size();
   }
   if (stage_ms) {
+    // with the blocks on several streams the Gram products overlap other
+    // blocks' reductions: [0] = the Gram products' own device time, [1] =
+    // the rest of the call's device time plus the host QL left at its end
     stage_ms[0] = t_gram;
-    stage_ms[1] = t_red + t_qr;  // GPU reduction plus the host QL left after the last block
+    stage_ms[1] = std::max(0.0, (double)t_all - t_gram) + t_qr;
   }
   double tot = 0.0;
   for (double v : wt) tot += v;

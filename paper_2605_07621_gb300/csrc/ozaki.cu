@@ -3,6 +3,8 @@
 // kernels here, tiles staged by TMA with 128-byte swizzle, products issued
 // by one thread with tcgen05.mma into FP32 accumulators in TMEM (one per
 // digit order), drained by four warps and combined in FP64.
+#include <atomic>
+
 #include "ozaki.h"
 
 #include <cmath>
@@ -593,10 +595,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 ed_status oz_gemm(OzContext* o, const OzProblem* d_probs, int nprob, long long tiles, double* y, cudaStream_t st) {
   if (tiles <= 0) return ED_OK;
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory opt-in, once per device (calls may come from several host threads)
+  static std::atomic<unsigned long long> attr_set{0};
+  const unsigned long long bit = 1ull << (o->device & 63);
+  if (!(attr_set.load() & bit)) {
     ED_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem));
-    attr = true;
+    attr_set.fetch_or(bit);
   }
   k_oz_gemm<<<(unsigned)tiles, kOzThreads, kOzSmem, st>>>(d_probs, nprob, o->d_maps, y, o->d_err);
   ED_CUDA_TRY(cudaGetLastError());
