@@ -101,6 +101,9 @@ def sum_over_ranks(value: float, world: int, device: str = "cpu") -> float:
 # 64; the BF16 FLOPs it executes are counted on those padded tiles.
 OZ_PAIRS = 36
 
+# pieces (and streams) per host<->device copy in the end-to-end pipeline
+E2E_CHUNKS = 4
+
 
 def oz_tensor_flops(M, N, K, tri=False):
     """BF16 FLOPs the tensor cores execute for one digit-split product."""
@@ -679,36 +682,47 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         serial = {"value": n_e2e / wall, "device_ms_per_step": e0.elapsed_time(e1) / n_e2e}
-        # the same steps pipelined over three streams (H2D of step i+1, H psi
-        # of step i and D2H of step i-1 overlap; two device buffer pairs)
+        # the same steps pipelined (H2D of step i+1, H psi of step i and D2H
+        # of step i-1 overlap; two device buffer pairs); each copy is split
+        # into E2E_CHUNKS pieces on as many streams, since one copy of a large
+        # buffer runs on a single copy engine
         xs, ys = [x, torch.empty_like(x)], [y, torch.empty_like(y)]
-        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(n_e2e)]
+        s_in = [torch.cuda.Stream() for _ in range(E2E_CHUNKS)]
+        s_out = [torch.cuda.Stream() for _ in range(E2E_CHUNKS)]
+        s_cmp = torch.cuda.Stream()
+        cb = -(-D // E2E_CHUNKS)
+        parts = [(q * cb, min(D, (q + 1) * cb)) for q in range(E2E_CHUNKS)]
+        ev_in = [[torch.cuda.Event() for _ in range(E2E_CHUNKS)] for _ in range(n_e2e)]
         ev_cmp = [torch.cuda.Event() for _ in range(n_e2e)]
-        ev_out = [torch.cuda.Event() for _ in range(n_e2e)]
+        ev_out = [[torch.cuda.Event() for _ in range(E2E_CHUNKS)] for _ in range(n_e2e)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(n_e2e):
             k = i % 2
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev_cmp[i - 2])
-                xs[k].copy_(xh, non_blocking=True)
-                ev_in[i].record(s_in)
+            for q, (a, b) in enumerate(parts):
+                with torch.cuda.stream(s_in[q]):
+                    if i >= 2:
+                        s_in[q].wait_event(ev_cmp[i - 2])
+                    xs[k][a:b].copy_(xh[a:b], non_blocking=True)
+                    ev_in[i][q].record(s_in[q])
             with torch.cuda.stream(s_cmp):
-                s_cmp.wait_event(ev_in[i])
-                if i >= 2:
-                    s_cmp.wait_event(ev_out[i - 2])
+                for q in range(E2E_CHUNKS):
+                    s_cmp.wait_event(ev_in[i][q])
+                    if i >= 2:
+                        s_cmp.wait_event(ev_out[i - 2][q])
                 ed.apply_H(ctx, xs[k], ys[k], stream=s_cmp)
                 ev_cmp[i].record(s_cmp)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_cmp[i])
-                yh.copy_(ys[k], non_blocking=True)
-                ev_out[i].record(s_out)
+            for q, (a, b) in enumerate(parts):
+                with torch.cuda.stream(s_out[q]):
+                    s_out[q].wait_event(ev_cmp[i])
+                    yh[a:b].copy_(ys[k][a:b], non_blocking=True)
+                    ev_out[i][q].record(s_out[q])
         torch.cuda.synchronize()
         wall_p = time.perf_counter() - t0
         e2e = {"value": n_e2e / wall_p, "unit": UNIT, "h2d_bytes_per_step": D * esz, "d2h_bytes_per_step": D * esz,
-               "steps": n_e2e, "pipelined": "H2D / H psi / D2H on three streams, two device buffer pairs",
+               "steps": n_e2e,
+               "pipelined": f"H2D / H psi / D2H overlapped, two device buffer pairs, each copy in {E2E_CHUNKS} "
+                            "pieces on as many streams",
                "serial": serial}
         del xh, yh, xs, ys
 
