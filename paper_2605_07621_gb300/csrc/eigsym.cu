@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256) k_pcol(const float2* __restrict__ F, long
   {
     const int k = threadIdx.x & (kKw - 1), hf = threadIdx.x >> 7;
     float2 s = z2;
-#pragma unroll 8
+#pragma unroll 16
     for (int b = hf; b < (int)gridDim.x; b += 2) df_add(s, cp[(long long)b * (kKw + 1) + k]);
     acc[hf][k] = s;
     if (warp == 0) {  // slot 2 nb (the sum of squares)
@@ -774,9 +774,9 @@ __global__ void __launch_bounds__(256) k_psum2(const float2* __restrict__ part, 
     float2 s = z2, corr = z2;
     if (i < m) {
       const int Ii = (i - u0) / kU;
-#pragma unroll 4
+#pragma unroll 8
       for (int J = q; J <= Ii; J += kPsT) df_add(s, part[(long long)J * ld + i]);
-#pragma unroll 4
+#pragma unroll 8
       for (int I = Ii + q; I < Tn; I += kPsT) df_add(s, part[(long long)(TU + I) * ld + i]);
       const float2* row = WVf + (long long)i * kKw;
 #pragma unroll 4
