@@ -8,13 +8,6 @@
 #include "ozaki.h"
 
 namespace edk {
-// Reduce the symmetric m x m row-major A (device; only its lower triangle,
-// diagonal included, is read and overwritten) to tridiagonal form; the
-// diagonal (m) and off-diagonal (m - 1) entries are
-// copied to the host arrays, asynchronously on `st` (synchronise before use).
-// work: device scratch of tridiag_work_doubles(m) doubles.
-inline long long tridiag_work_doubles(int m) { return 8LL * m + 2LL * ((m + 31) / 32) * m; }
-ed_status tridiag_reduce(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st, int sms);
 // Blocked reduction: panels of kTriNb reflectors, each followed by the
 // trailing update A -= V W^T + W V^T as one FP64-accurate tensor-core product
 constexpr int kTriNb = 64;
@@ -50,6 +43,11 @@ ed_status tridiag_blocked_setup(OzContext* oz, double* A, int m, const OzOperand
 inline long long tridiag_blocked_work_doubles(int m) {
   return 6LL * m + 2LL * ((m + 63) / 64) * m + 128LL * (2 * kTriNb + 1) + 2 * kTriNb + 4096 + 1024 + 8;
 }
+// Reduce the symmetric m x m row-major A (device; only its lower triangle,
+// diagonal included, is read and overwritten) to tridiagonal form; the
+// diagonal (m) and off-diagonal (m - 1) entries are copied to the host
+// arrays (pinned), asynchronously on `st` (wait on the stream before use).
+// work: device scratch of tridiag_blocked_work_doubles(m) doubles.
 ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host, double* e_host, cudaStream_t st,
                                  int sms, const TriBlocked& tb);
 // all eigenvalues of the tridiagonal (d, e) into d (unordered); false if the

@@ -103,7 +103,7 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
   auto lane_bytes = [&](long long m, long long xel) {
     const long long ldF = tridiag_ldF((int)m);
     return (double)m * m * 8 + (double)m * ldF * 8 + 3.0 * m * 2 * kTriNb * 8 +
-           8.0 * std::max(tridiag_work_doubles((int)m), tridiag_blocked_work_doubles((int)m)) +
+           8.0 * tridiag_blocked_work_doubles((int)m) +
            2.0 * kOzDigits * xel + 2.0 * 2 * kOzDigits * m * 2 * kTriNb + 4.0 * m;
   };
   int lanes = kLanes;
@@ -155,9 +155,7 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     }
     const long long mk = L[k].mmax;
     ED_TRY(mem.get((void**)&L[k].G, (size_t)mk * mk * sizeof(double)));
-    ED_TRY(mem.get((void**)&L[k].work, (size_t)std::max(tridiag_work_doubles((int)mk),
-                                                        tridiag_blocked_work_doubles((int)mk)) *
-                                           sizeof(double)));
+    ED_TRY(mem.get((void**)&L[k].work, (size_t)tridiag_blocked_work_doubles((int)mk) * sizeof(double)));
     ED_TRY(mem.get((void**)&L[k].F, (size_t)mk * tridiag_ldF((int)mk) * sizeof(float2)));
     ED_TRY(mem.get((void**)&L[k].WVf, (size_t)mk * 2 * kTriNb * sizeof(float2)));
     ED_TRY(oz_alloc(&oz, (void**)&L[k].NVW, (size_t)mk * 2 * kTriNb * sizeof(double)));
