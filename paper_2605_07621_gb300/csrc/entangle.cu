@@ -304,55 +304,65 @@ extern "C" ed_status ed_entanglement_spectrum(ed_ctx* c, const double* psi, doub
     }
     fcv.notify_all();
   };
-  for (int k = 0; k < lanes; ++k) {
-    workers.emplace_back([&, k] {
-      auto fail = [&](ed_status s) {
-        lst[k] = s;
-        lmsg[k] = ed_last_error();
-        if (k == 0) first_set(2);
-      };
-      DeviceGuard dg(c->device);
-      if (dg.status() != ED_OK) return fail(ED_ECUDA);
-      Lane& ln = L[k];
-      if (k > 0) {
-        std::unique_lock<std::mutex> lk(fm);
-        fcv.wait(lk, [&] { return first_state != 0; });
-        if (first_state == 2) return;
-        lk.unlock();
-        if (cudaStreamWaitEvent(ln.s, ev_se.e[2], 0) != cudaSuccess) return fail(ED_ECUDA);
+  auto lane_fn = [&](int k) {
+    auto fail = [&](ed_status s) {
+      lst[k] = s;
+      lmsg[k] = ed_last_error();
+      if (k == 0) first_set(2);
+    };
+    DeviceGuard dg(c->device);
+    if (dg.status() != ED_OK) return fail(ED_ECUDA);
+    Lane& ln = L[k];
+    if (k > 0) {
+      std::unique_lock<std::mutex> lk(fm);
+      fcv.wait(lk, [&] { return first_state != 0; });
+      if (first_state == 2) return;
+      lk.unlock();
+      if (cudaStreamWaitEvent(ln.s, ev_se.e[2], 0) != cudaSuccess) return fail(ED_ECUDA);
+    }
+    for (size_t bi : lane_blocks[k]) {
+      const Block& b = c->blocks[bi];
+      const int m = (int)bm(bi);
+      double* hd = hde.p + hoff[bi];
+      double* he = hd + std::max(m, 1);
+      ed_status s = ED_OK;
+      if (cudaEventRecord(ev_g0.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+      if ((s = oz_slice(&oz, d_jobs + bi, 1, units[bi], b.dA > b.dB, nullptr, ln.s)) != ED_OK) return fail(s);
+      if ((s = oz_gemm(&oz, d_probs + bi, 1, tiles[bi], nullptr, ln.s)) != ED_OK) return fail(s);
+      if (cudaEventRecord(ev_g1.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+      TriBlocked tb{&oz, ln.NVW, ln.WV, ln.WVf, ln.F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi],
+                    d_tprobs + toff[bi]};
+      if (m >= 3 && (s = tmap_8b_2d(&tb.tmF, ln.F, m, m, tb.ldF, 34, 32)) != ED_OK) return fail(s);
+      if ((s = tridiag_reduce_blocked(ln.G, m, ln.work, hd, he, ln.s, sms, tb)) != ED_OK) return fail(s);
+      if (cudaEventRecord(ev_done.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+      if (k == 0 && bi == lane_blocks[0][0]) {
+        if (cudaEventRecord(ev_se.e[2], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+        first_set(1);
       }
-      for (size_t bi : lane_blocks[k]) {
-        const Block& b = c->blocks[bi];
-        const int m = (int)bm(bi);
-        double* hd = hde.p + hoff[bi];
-        double* he = hd + std::max(m, 1);
-        ed_status s = ED_OK;
-        if (cudaEventRecord(ev_g0.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
-        if ((s = oz_slice(&oz, d_jobs + bi, 1, units[bi], b.dA > b.dB, nullptr, ln.s)) != ED_OK) return fail(s);
-        if ((s = oz_gemm(&oz, d_probs + bi, 1, tiles[bi], nullptr, ln.s)) != ED_OK) return fail(s);
-        if (cudaEventRecord(ev_g1.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
-        TriBlocked tb{&oz, ln.NVW, ln.WV, ln.WVf, ln.F, tridiag_ldF(m), {}, oz.d_err, d_tjobs + 2 * toff[bi],
-                      d_tprobs + toff[bi]};
-        if (m >= 3 && (s = tmap_8b_2d(&tb.tmF, ln.F, m, m, tb.ldF, 34, 32)) != ED_OK) return fail(s);
-        if ((s = tridiag_reduce_blocked(ln.G, m, ln.work, hd, he, ln.s, sms, tb)) != ED_OK) return fail(s);
-        if (cudaEventRecord(ev_done.e[bi], ln.s) != cudaSuccess) return fail(ED_ECUDA);
-        if (k == 0 && bi == lane_blocks[0][0]) {
-          if (cudaEventRecord(ev_se.e[2], ln.s) != cudaSuccess) return fail(ED_ECUDA);
-          first_set(1);
+      cudaEvent_t done = ev_done.e[bi];
+      auto ql = [&dd, &ee, &ok, hd, he, m, bi, done] {
+        if (cudaEventSynchronize(done) != cudaSuccess) {
+          ok[bi] = 2;
+          return;
         }
-        cudaEvent_t done = ev_done.e[bi];
-        qr[k].emplace_back([&dd, &ee, &ok, hd, he, m, bi, done] {
-          if (cudaEventSynchronize(done) != cudaSuccess) {
-            ok[bi] = 2;
-            return;
-          }
-          dd[bi].assign(hd, hd + m);
-          ee[bi].assign(he, he + std::max(m - 1, 0));
-          ok[bi] = tridiag_eigenvalues(dd[bi], ee[bi]) ? 1 : 0;
-        });
+        dd[bi].assign(hd, hd + m);
+        ee[bi].assign(he, he + std::max(m - 1, 0));
+        ok[bi] = tridiag_eigenvalues(dd[bi], ee[bi]) ? 1 : 0;
+      };
+      try {
+        qr[k].emplace_back(ql);
+      } catch (...) {
+        ql();  // no thread to be had: wait for the block and reduce it here
       }
-      if (cudaEventRecord(ev_lane.e[k], ln.s) != cudaSuccess) return fail(ED_ECUDA);
-    });
+    }
+    if (cudaEventRecord(ev_lane.e[k], ln.s) != cudaSuccess) return fail(ED_ECUDA);
+  };
+  for (int k = 0; k < lanes; ++k) {
+    try {
+      workers.emplace_back(lane_fn, k);
+    } catch (...) {
+      lane_fn(k);  // no thread to be had: enqueue this lane from here
+    }
   }
   for (auto& x : workers) x.join();
   for (int k = 0; k < lanes; ++k)
