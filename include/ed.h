@@ -204,10 +204,13 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  * sum_{s,i} lambda_{s,i}.  rho_A is block diagonal, rho_A(s) = Psi_s Psi_s^T;
  * its nonzero eigenvalues are those of the Gram matrix of Psi_s in the
  * smaller of d_A(s), d_B(s), formed on the device by this library; its
- * eigenvalues come from a Householder reduction to tridiagonal form on the
- * device and implicit QL steps on the host (one host thread per block, in
- * parallel with the device work of the next block; ED_ENOCONV if a QL
- * iteration does not converge).
+ * eigenvalues come from a blocked Householder reduction to tridiagonal form
+ * on the device (float-float panel arithmetic, FP64-accurate tensor-core
+ * trailing updates) and implicit QL steps on the host (one host thread per
+ * block as soon as its tridiagonal matrix is ready; ED_ENOCONV if a QL
+ * iteration does not converge).  The largest block is reduced first and
+ * alone, the others concurrently on up to three internal streams that start
+ * after the caller's prior work on `stream`.
  *   psi      device FP64 vector of ctx (not normalised by the call)
  *   lambda   host, capacity cap: for every block in ed_blocks order, its
  *            min(d_A, d_B) eigenvalues in descending order (rounding can
@@ -217,17 +220,19 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  *   weight   host, one per block (nullable): ||Psi_s||^2 = trace rho_A(s),
  *            summed on the device in FP64
  *   entropy  host (nullable): -sum p ln p over p = lambda / sum(weight) > 0
- *   stage_ms host (nullable), 2 doubles: device time of the Gram kernels, and
- *            the device time of the tridiagonal reductions plus the host QL
- *            time left after the last block (milliseconds)
+ *   stage_ms host (nullable), 2 doubles: the Gram kernels' own device time
+ *            (summed over blocks; they overlap other blocks' reductions),
+ *            and the rest of the call's device time plus the host QL time
+ *            left after the device work (milliseconds)
  * The Gram matrices are formed on the tensor cores in FP64-accurate
  * digit-split form (8 BF16 digit planes per value, exact FP32 sums per digit
- * order, FP64 combination).  Device memory: one Gram matrix of the largest
- * block (8 min(dA,dB)^2 bytes; only its lower triangle is formed and
- * reduced), the digit planes of one block (16 bytes per element) and the
- * reduction's workspace (about m^2 / 2 bytes for the largest m = min(dA,dB));
- * blocks with min(dA,dB) > 46340 are ED_EUNSUPPORTED.  Synchronises the
- * stream. */
+ * order, FP64 combination).  Device memory, per stream sized for its largest
+ * block m = min(dA,dB) with the larger dimension L: the Gram matrix
+ * (8 m^2 bytes; only its lower triangle is formed and reduced), its
+ * float-float copy (8 m^2 bytes), the digit planes of Psi_s (16 m L bytes)
+ * and the panel and work arrays (about 2.3 KB x m plus m^2 / 4 bytes); fewer
+ * streams are used when device memory is short.  Blocks with
+ * min(dA,dB) > 46340 are ED_EUNSUPPORTED.  Synchronises the stream. */
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
                                    double* weight, double* entropy, double* stage_ms, void* stream);
 

@@ -294,7 +294,7 @@ class EntanglementSpectrum:
     lam: list            # per block: eigenvalues of rho_A(s) = Psi_s Psi_s^T, descending
     weight: np.ndarray   # per block: ||Psi_s||^2 (trace of rho_A(s))
     entropy: float       # -sum p ln p of the normalised spectrum
-    stage_ms: tuple      # device ms of the Gram kernels and of the eigensolver
+    stage_ms: tuple      # ms: the Gram kernels' device time; the rest of the call (device + host QL tail)
 
 
 def entanglement_spectrum(ctx: Context, psi, stream=None) -> EntanglementSpectrum:
