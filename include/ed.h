@@ -230,7 +230,7 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
  * block m = min(dA,dB) with the larger dimension L: the Gram matrix
  * (8 m^2 bytes; only its lower triangle is formed and reduced), its
  * float-float copy (8 m^2 bytes), the digit planes of Psi_s (16 m L bytes)
- * and the panel and work arrays (about 2.3 KB x m plus m^2 / 4 bytes); fewer
+ * and the panel and work arrays (about 7 KB x m plus m^2 / 4 bytes); fewer
  * streams are used when device memory is short.  Blocks with
  * min(dA,dB) > 46340 are ED_EUNSUPPORTED.  Synchronises the stream. */
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
