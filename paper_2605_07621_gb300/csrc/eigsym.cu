@@ -870,72 +870,60 @@ ed_status tridiag_blocked_setup(OzContext* oz, double* A, int m, const OzOperand
   return ED_OK;
 }
 
-// All eigenvalues of the symmetric tridiagonal matrix (d, e) by implicit QL
-// steps (Bowdler, Martin, Reinsch and Wilkinson, "The QR and QL algorithms
-// for symmetric matrices", Numer. Math. 11, 1968): for the unreduced block
-// starting at row l, a shift from its leading 2 x 2, then plane rotations
-// chased from the bottom of the block up, in the recurrences that carry the
-// running quantities (g, p) instead of forming each rotated 2 x 2 -- the
-// numerically favoured form.  e[i] couples i and i+1; d is overwritten with
-// the eigenvalues (unordered), each within a few eps of the matrix norm.
-// false if a block needs more than 60 steps.
-// sqrt(a^2 + b^2); std::hypot's overflow and underflow guard only where the
-// squares could leave the FP64 range (it costs several times a square root)
-static inline double qhypot(double a, double b) {
-  const double m = std::max(std::fabs(a), std::fabs(b));
-  if (m > 0x1p+500 || (m < 0x1p-500 && m > 0.0)) return std::hypot(a, b);
-  return std::sqrt(a * a + b * b);
-}
-
+// All eigenvalues of the symmetric tridiagonal matrix (d, e) by the
+// root-free QL iteration (Pal, Walker and Kahan; Reinsch, "A stable,
+// rational QR algorithm for the computation of the eigenvalues of an
+// Hermitian, tridiagonal matrix", Math. Comp. 25, 1971; Parlett, The
+// Symmetric Eigenvalue Problem, Sec. 8.15): the implicitly shifted QL sweep
+// written in the squared off-diagonals e_i^2, so a rotation costs one
+// reciprocal and one division and no square root.  For the unreduced block
+// starting at row l: the shift is the eigenvalue of its leading 2 x 2 nearer
+// d[l], the sweep runs from the bottom of the block up.  e[i] couples i and
+// i+1; d is overwritten with the eigenvalues (unordered), each within a few
+// eps of the matrix norm.  false if a block needs more than 60 sweeps.
 bool tridiag_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
   const int n = (int)d.size();
   if (n <= 1) return true;
-  e.resize(n);
-  e[n - 1] = 0.0;
-  const double eps = std::ldexp(1.0, -53);
+  const double eps = std::ldexp(1.0, -53), eps2 = eps * eps;
   // an off-diagonal counts as zero below eps times its neighbours or below
   // eps times the norm of the whole matrix (eigenvalues far below the norm,
   // here the many vanishing ones of a Gram matrix, are resolved absolutely)
   double tnorm = 0.0;
   for (int i = 0; i < n; ++i)
-    tnorm = std::max(tnorm, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) + std::fabs(e[i]));
-  const double tiny = eps * tnorm;
+    tnorm = std::max(tnorm, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) +
+                                (i < n - 1 && i < (int)e.size() ? std::fabs(e[i]) : 0.0));
+  const double tiny2 = (eps * tnorm) * (eps * tnorm);
+  std::vector<double> e2(n, 0.0);
+  for (int i = 0; i < n - 1; ++i) e2[i] = e[i] * e[i];
   for (int l = 0; l < n; ++l) {
     for (int iter = 0;; ++iter) {
       int m = l;  // end of the unreduced block that starts at l
-      while (m < n - 1 && std::fabs(e[m]) > eps * (std::fabs(d[m]) + std::fabs(d[m + 1])) && std::fabs(e[m]) > tiny)
+      while (m < n - 1) {
+        const double s = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (e2[m] <= eps2 * s * s || e2[m] <= tiny2) break;
         ++m;
+      }
       if (m == l) break;
       if (iter == 60) return false;
       // shift: the eigenvalue of the leading 2 x 2 nearer d[l]
-      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = qhypot(g, 1.0);
-      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
-      double s = 1.0, c = 1.0, p = 0.0;
-      bool split = false;
+      const double rte = std::sqrt(e2[l]);
+      double sigma = (d[l + 1] - d[l]) / (2.0 * rte);
+      sigma = d[l] - rte / (sigma + std::copysign(std::hypot(sigma, 1.0), sigma));
+      // the sweep, bottom up: rotation i carries c, s (as squares) and gamma
+      double c = 1.0, s = 0.0, gamma = d[m] - sigma, p = gamma * gamma;
       for (int i = m - 1; i >= l; --i) {
-        const double f = s * e[i], b = c * e[i];
-        r = qhypot(f, g);
-        e[i + 1] = r;
-        if (r == 0.0) {  // the rotation vanished: the block splits at i + 1
-          d[i + 1] -= p;
-          e[m] = 0.0;
-          split = true;
-          break;
-        }
-        const double ri = 1.0 / r;
-        s = f * ri;
-        c = g * ri;
-        g = d[i + 1] - p;
-        r = (d[i] - g) * s + 2.0 * c * b;
-        p = s * r;
-        d[i + 1] = g + p;
-        g = c * r - b;
+        const double bb = e2[i], r = p + bb;
+        if (i != m - 1) e2[i + 1] = s * r;
+        const double oldc = c, ri = 1.0 / r;
+        c = p * ri;
+        s = bb * ri;
+        const double oldgam = gamma, alpha = d[i];
+        gamma = c * (alpha - sigma) - s * oldgam;
+        d[i + 1] = oldgam + (alpha - gamma);
+        p = c != 0.0 ? gamma * gamma / c : oldc * bb;
       }
-      if (split) continue;
-      d[l] -= p;
-      e[l] = g;
-      e[m] = 0.0;
+      e2[l] = s * p;
+      d[l] = sigma + gamma;
     }
   }
   return true;
