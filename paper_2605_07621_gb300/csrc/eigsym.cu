@@ -587,13 +587,12 @@ __global__ void __launch_bounds__(32 * kSvWarps) k_symv(const __grid_constant__ 
 }
 
 // p[i] for rows i >= r0 (pf, float-float, in the scaled matrix; vf[i] becomes
-// v = tau vf): the unit
-// slots that k_symv wrote (row slots 0..I(i), column slots TU + I(i) .. TU +
-// Tn - 1, units from u0), minus the panel's pending terms
-// V ((sigma W)^T v) + (sigma W) (V^T v); kPsT threads per row.  Per CTA: the
-// partial sum of p.v; the last CTA to finish (a ticket on *ctr) adds them in
-// a fixed order into K = beta^2 p.v / 2 (*Kp, FP64, and *Kf), which makes
-// w = beta p - K v.
+// v = tau vf): the unit slots that k_symv wrote (row slots 0..I(i), column
+// slots TU + I(i) .. TU + Tn - 1, units from u0), minus the panel's pending
+// terms V ((sigma W)^T v) + (sigma W) (V^T v); kPsT threads per row.  Per
+// CTA: the partial sum of p.v; the last CTA to finish (a ticket on *ctr)
+// adds them in a fixed order into K = beta^2 p.v / 2 (*Kf, float-float),
+// which makes w = beta p - K v.
 __global__ void __launch_bounds__(256) k_psum2(const float2* __restrict__ part, int m, int r0, int u0, int TU, int Tn,
                                                const float2* __restrict__ WVf, const float2* __restrict__ tu, int j,
                                                float2* __restrict__ vf, const float2* tauf, float2* __restrict__ pf,
@@ -770,7 +769,7 @@ ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host,
   if (m <= 0) return ED_OK;
   auto cdiv = [](long long a, long long b) { return (a + b - 1) / b; };
   const int TU = (int)cdiv(m, kU);
-  float2* vf = reinterpret_cast<float2*>(work);          // sigma v of the latest column
+  float2* vf = reinterpret_cast<float2*>(work);          // the latest column's x, then its v
   float2* pf = reinterpret_cast<float2*>(work + m);      // its p (scaled)
   double* beta = work + 2 * m;
   float2* betaf = reinterpret_cast<float2*>(work + 3 * m);
@@ -778,7 +777,7 @@ ed_status tridiag_reduce_blocked(double* A, int m, double* work, double* d_host,
   double* e = work + 5 * m;
   float2* part = reinterpret_cast<float2*>(work + 6 * m);  // 2 TU slots of m
   float2* cp = part + 2LL * TU * m;                         // k_pcol partials (kPcolCtas x (2 nb + 1))
-  float2* tu = cp + (long long)kPcolCtas * (kKw + 1);       // W^T v, (sigma V)^T v (2 nb)
+  float2* tu = cp + (long long)kPcolCtas * (kKw + 1);       // (sigma W)^T v, V^T v (2 nb)
   float2* pvp = tu + kKw;                                   // p.v partials (kRowCtas)
   auto* amx = reinterpret_cast<unsigned long long*>(pvp + kRowCtas);  // kAmaxCtas
   float2* Kf = reinterpret_cast<float2*>(amx + kAmaxCtas);  // K of the latest column
