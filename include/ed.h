@@ -236,6 +236,17 @@ ed_status ed_lanczos_gf(ed_ctx* ctx, const void* psi0, double e0, int site, int 
 ed_status ed_entanglement_spectrum(ed_ctx* ctx, const double* psi, double* lambda, int64_t cap, int64_t* n_lambda,
                                    double* weight, double* entropy, double* stage_ms, void* stream);
 
+/* The last stage of ed_entanglement_spectrum on its own: all eigenvalues of
+ * the n x n symmetric tridiagonal matrix with diagonal d[0..n-1] and
+ * off-diagonal e[0..n-2] (e[i] couples i and i+1), by the root-free implicit
+ * QL iteration on the host (Pal, Walker and Kahan; Reinsch 1971), into
+ * lambda[0..n-1] in ascending order; each within a few eps of the matrix
+ * norm.  Host arrays, owned by the caller; d and e are not modified; lambda
+ * may not alias them.  n = 0 is a no-op.  ED_EINVAL for n < 0 or a NULL
+ * array (e may be NULL for n <= 1); ED_ENOCONV if a block needs more than 60
+ * QL sweeps.  Needs no device. */
+ed_status ed_tridiag_eigenvalues(const double* d, const double* e, int64_t n, double* lambda);
+
 /* ---- dense-block form -----------------------------------------------------
  * The bipartite operator of paper Eq. (2) with dense side operators on
  * symmetry blocks (its DMRG setting): blocks q = 0..nq-1 of dimension

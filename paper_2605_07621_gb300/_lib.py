@@ -72,6 +72,7 @@ SIGNATURES = [
                               c_void_p]),
     ("ed_entanglement_spectrum", c_int, [c_void_p, c_void_p, c_void_p, c_int64, P(c_int64), c_void_p, c_void_p,
                                          c_void_p, c_void_p]),
+    ("ed_tridiag_eigenvalues", c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     ("ed_dense_create", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                 P(c_void_p)]),
     ("ed_dense_dim", c_int64, [c_void_p]),

@@ -929,3 +929,23 @@ bool tridiag_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
 }
 
 }  // namespace edk
+
+extern "C" ed_status ed_tridiag_eigenvalues(const double* d, const double* e, int64_t n, double* lambda) {
+  if (n < 0 || (n > 0 && (!d || !lambda)) || (n > 1 && !e)) {
+    edk::set_error("ed_tridiag_eigenvalues: n < 0 or a NULL array");
+    return ED_EINVAL;
+  }
+  if (n == 0) return ED_OK;
+  if (n > (int64_t)1 << 30) {
+    edk::set_error("ed_tridiag_eigenvalues: n = %lld is too large", (long long)n);
+    return ED_EINVAL;
+  }
+  std::vector<double> dd(d, d + n), ee(n > 1 ? e : d, n > 1 ? e + (n - 1) : d);
+  if (!edk::tridiag_eigenvalues(dd, ee)) {
+    edk::set_error("ed_tridiag_eigenvalues: the QL iteration did not converge");
+    return ED_ENOCONV;
+  }
+  std::sort(dd.begin(), dd.end());
+  std::copy(dd.begin(), dd.end(), lambda);
+  return ED_OK;
+}
